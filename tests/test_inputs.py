@@ -1,0 +1,52 @@
+"""Seeded input generator: published splitmix64 vectors, Box-Muller moments, layout."""
+import math
+
+import numpy as np
+
+import rsw_inputs as ri
+
+
+def test_splitmix64_published_vectors():
+    # Outputs of the reference splitmix64 for seeds 0 and 1234567 (the vectors
+    # used by the reference C implementation and java.util.SplittableRandom tests).
+    g = ri.SplitMix64(0)
+    assert g.next_u64() == 0xE220A8397B1DCDAF
+    g = ri.SplitMix64(1234567)
+    assert [g.next_u64() for _ in range(3)] == [6457827717110365317, 3203168211198807973,
+                                                9817491932198370423]
+
+
+def test_uniform_open_interval_and_normal_moments():
+    g = ri.SplitMix64(7)
+    xs = np.array([g.normal_pair() for _ in range(20000)]).ravel()
+    assert abs(xs.mean()) < 0.03
+    assert abs(xs.var() - 1.0) < 0.03
+    u = [ri.SplitMix64(s).uniform() for s in range(200)]
+    assert min(u) > 0.0 and max(u) < 1.0
+
+
+def test_spectrum_layout_and_determinism():
+    n = 64
+    a = ri.random_spectrum(n, 8, 16.0, 0)
+    b = ri.random_spectrum(n, 8, 16.0, 0)
+    assert a.shape == (3, n // 2 + 1) and a.dtype == np.complex128
+    np.testing.assert_array_equal(a, b)
+    assert np.all(a[:, 9:] == 0)
+    assert np.all(a[:, 0].imag == 0)
+    # amplitude convention: X_k = N u_k has E|X_k|^2 = exp(-2k^2/16)
+    big = ri.random_batch(n, 8, 16.0, 400, 100)
+    for k in (1, 4):
+        m2 = np.mean(np.abs(n * big[:, :, k]) ** 2)
+        assert abs(m2 / math.exp(-2 * k * k / 16.0) - 1.0) < 0.15
+    c = ri.random_spectrum(n, 8, 16.0, 1)
+    assert not np.allclose(a, c)
+
+
+def test_workloads():
+    w = ri.SMALL_N64
+    assert math.isclose(w.dT, 1.0 / 16)
+    insts = ri.uneven_instances(64)
+    assert {i.n_grid for i in insts} <= {64, 128, 256, 512, 1024}
+    assert all(1e-4 <= i.eps <= 1e-2 for i in insts)
+    assert {i.slices for i in insts} <= {32, 64, 128}
+    assert [i.seed for i in insts[:3]] == [1000, 1001, 1002]
