@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the asymptotic parareal hot path on one GB300.
+
+Workload (the single large instance): 1D rotating shallow water, N = 512
+grid points, eps = 1e-3, nu = 1e-4, T = 10 over 256 slices, fine ETDRK4 step
+dt = 1e-4 (391 steps of 9.99e-5 per slice), M = 64 quadrature points, seeded
+synthetic initial spectrum (|k| <= 32, scale e^{-k^2/256}).
+
+One timed step = one parareal iteration k >= 1 through the C ABI
+(arp_parareal_iterate): the fine sweep of all 256 slices, V = F - G, the
+serial chain of 256 coarse steps and the convergence norm.  Metric: fine
+grid-point-steps per second = slices * N * fine steps / step time.
+
+--impl reference times the FP64 CPU oracle instead (one iteration restricted
+to 8 slices per step, on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import rsw_inputs as ri  # noqa: E402
+
+WORKLOAD = ri.LARGE_N512
+METRIC = "fine grid-pt-steps/s"
+# FP32 peak of the plain ALUs: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz.
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP64 peak: the part's nominal 1.25 TFLOP/s (FP64 units are a small fraction of FP32 ones).
+FP64_ALU_PEAK_TFLOPS = 1.25
+CPU_SAMPLE_SLICES = 8
+
+
+def flops_per_grid_pt_step(n_grid: int) -> float:
+    """Algorithmic flops of one ETDRK4 step per grid point: 4 evaluations of N,
+    each 7 real FFTs at 2.5 N log2 N, plus 52 N for rotations, derivatives and
+    products; plus 80 N for the exponential combination."""
+    return 70.0 * math.log2(n_grid) + 288.0
+
+
+def fine_steps(dT: float, dt: float) -> int:
+    return max(1, int(math.ceil(dT / dt - 1e-9)))
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank: int, world: int) -> dict | None:
+    import torch
+    import torch.distributed as dist
+
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(bld.LIB):
+        bld.build()
+    if world > 1:
+        dist.barrier()
+    b.load_library()
+    w = WORKLOAD
+    steps = fine_steps(w.dT, w.dt)
+    units = w.slices * w.n_grid * steps  # fine grid-point-steps per iteration
+    prec = b.ARP_FP32 if args.precision == "fp32" else b.ARP_FP64
+    H = w.n_grid // 2 + 1
+    solver = b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec)
+    ctx = solver.ctx
+    stream = torch.cuda.current_stream()
+    u0 = torch.from_numpy(w.initial_state()).cuda()
+    b.arp_set_initial(ctx, u0)
+    b.arp_parareal_iterate(ctx)                    # predictor, untimed
+    for _ in range(args.warmup):
+        b.arp_parareal_iterate(ctx)
+    # inputs are far smaller than L2 (129 MB): flush L2 between timed steps
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    changes = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        _, ch = b.arp_parareal_iterate(ctx)
+        ev[i][1].record(stream)
+        changes.append(ch)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(z) for a, z in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = units * args.steps * world / (total_ms / 1e3)
+
+    # dominant kernel: the fine sweep over all slices, timed live with events on its stream
+    U = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
+    b.arp_get_slices(ctx, U)
+    Fin = U[:-1].contiguous()
+    Fout = torch.empty_like(Fin)
+    b.arp_fine_batch(ctx, Fin, Fout)
+    reps = 5
+    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, z in fe:
+        flush.zero_()
+        a.record(stream)
+        b.arp_fine_batch(ctx, Fin, Fout)
+        z.record(stream)
+    torch.cuda.synchronize()
+    fine_ms = statistics.mean(a.elapsed_time(z) for a, z in fe)
+    flops = units * flops_per_grid_pt_step(w.n_grid)
+    achieved = flops / (fine_ms / 1e3) / 1e12
+    peak = FP32_ALU_PEAK_TFLOPS if prec == b.ARP_FP32 else FP64_ALU_PEAK_TFLOPS
+
+    # end to end through the public API with host buffers: one complete solve per step
+    # (u0 from pinned host memory, predictor + KMAX iterations, all slices back to pinned host)
+    u0h = torch.from_numpy(w.initial_state()).pin_memory()
+    Uh = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128).pin_memory()
+    kmax = w.k_max
+    b.arp_set_option(ctx, b.ARP_OPT_KMAX, kmax)
+    e2e_reps = 2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        b.arp_set_initial(ctx, u0h)
+        b.arp_parareal_solve(ctx)
+        b.arp_get_slices(ctx, Uh)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_reps
+    e2e_value = kmax * units * world / e2e_s
+
+    solver.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC,
+        "value": value,
+        "unit": "grid-pt-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == b.ARP_FP32 else "f64",
+        "data": "synthetic (seeded spectra; no dataset in the paper)",
+        "config": {"workload": w.name, "N": w.n_grid, "eps": w.eps, "nu": w.nu, "T": w.t_end,
+                   "slices": w.slices, "dt": w.dt, "fine_steps_per_slice": steps, "M": w.m_quad,
+                   "step": "one parareal iteration (fine sweep + correction + serial coarse chain + norm)",
+                   "precision": ("fp32 bulk, fp64 correction/norm/phases" if prec == b.ARP_FP32 else "fp64"),
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "fine_sweep_kernel", "launch_ms": fine_ms,
+                     "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec == b.ARP_FP32
+                                     else "FP64 nominal 1.25 TFLOP/s")},
+        "fine_only": {"value": units / (fine_ms / 1e3), "unit": "grid-pt-steps/s", "ms": fine_ms},
+        "e2e": {"value": e2e_value, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": int(u0h.numel() * 16),
+                "d2h_bytes_per_step": int(Uh.numel() * 16),
+                "step": f"complete solve: predictor + {kmax} iterations, host buffers", "seconds": e2e_s},
+        "gpu_launches": args.steps * (5 * w.slices + 4),
+        "clocks": clk,
+        "last_rel_change": changes[-1] if changes else None,
+    }
+
+
+# ----------------------------------------------------------------------------- oracle on the host
+
+def oracle_iteration_sample(slices: int):
+    """One parareal iteration of the FP64 oracle on the first `slices` slices of
+    the workload, starting from the predictor; returns (seconds, units)."""
+    import numpy as np  # noqa: F401
+
+    from oracle import rsw as o
+    w = WORKLOAD
+    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+    u0 = o.project(w.initial_state(), w.n_grid)
+    U = [u0]
+    for _ in range(slices):
+        U.append(o.coarse_step(U[-1], p))
+    import numpy as np
+    U = np.stack(U)
+    t0 = time.perf_counter()
+    f_old = o.fine_propagate(U[:-1], p)
+    g_old = o.coarse_step(U[:-1], p)
+    new = [u0]
+    for n in range(1, slices + 1):
+        new.append(o.coarse_step(new[n - 1], p) + f_old[n - 1] - g_old[n - 1])
+    dt = time.perf_counter() - t0
+    return dt, slices * w.n_grid * fine_steps(w.dT, w.dt)
+
+
+def cpu_cores_used() -> int:
+    # numpy's FFT and the oracle's elementwise work are single-threaded
+    return 1
+
+
+def run_reference(args, rank: int) -> dict | None:
+    if rank != 0:
+        return None
+    w = WORKLOAD
+    times, units = [], 0
+    for i in range(args.warmup + args.steps):
+        dt, units = oracle_iteration_sample(CPU_SAMPLE_SLICES)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = units * args.steps / total
+    sample = (f"one parareal iteration (fine sweep + G + serial chain) on {CPU_SAMPLE_SLICES} of "
+              f"{w.slices} slices per step")
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "grid-pt-steps/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded spectra; no dataset in the paper)",
+        "config": {"workload": w.name, "N": w.n_grid, "eps": w.eps, "nu": w.nu, "T": w.t_end,
+                   "slices": w.slices, "dt": w.dt, "M": w.m_quad,
+                   "step": sample},
+        "cpu_baseline": {"value": value, "unit": "grid-pt-steps/s", "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if out is not None:
+        if world == 1 and not args.no_cpu_baseline:
+            dt, units = oracle_iteration_sample(CPU_SAMPLE_SLICES)
+            out["cpu_baseline"] = {"value": units / dt, "unit": "grid-pt-steps/s", "cores": cpu_cores_used(),
+                                   "kind": "oracle",
+                                   "sample": f"one FP64 oracle parareal iteration on {CPU_SAMPLE_SLICES} of "
+                                             f"{WORKLOAD.slices} slices ({dt:.1f} s)"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * arp.h -- C ABI of the asymptotic parareal library for the 1D rotating
+ * shallow-water system (Haut & Wingate, "An asymptotic parallel-in-time
+ * method for highly oscillatory PDEs").
+ *
+ * Model (Sec. 6.1, Eq. 6.1 in the generic form of Eq. 1.1):
+ *     du/dt + (1/eps) L u = N(u) + D u,   u = (v1, v2, h), x in [0, 2 pi) periodic,
+ *     L_k = [[0, -1, i k F^-1/2], [1, 0, 0], [i k F^-1/2, 0, 0]]  (Fourier symbol),
+ *     D_k = -nu k^4,   N(u) = -(v1 v1_x, v1 v2_x, (h v1)_x).
+ *
+ * STATE LAYOUT (every state buffer of this API):
+ *     double, complex interleaved (re, im), shape [batch][3][H], H = N/2 + 1,
+ *     field order (v1, v2, h), entry [b][f][k] = coefficient u_k of field f with
+ *     u_f(x_j) = sum_{k=-N/2+1}^{N/2} u_k e^{i k x_j}, x_j = 2 pi j / N, and
+ *     u_{-k} = conj(u_k).  The state space keeps wavenumbers k <= K = (N-1)/3
+ *     (2/3 rule); inputs are projected onto it (bins above K are ignored and the
+ *     imaginary parts of the k = 0 bins are taken as zero); outputs have exact
+ *     zeros above K.
+ *
+ * OWNERSHIP: the caller owns every buffer passed in; the context owns its
+ *     tables, workspaces and the parareal iterates.  Unless a function says
+ *     otherwise, pointers are device pointers and work is enqueued on `stream`
+ *     (a cudaStream_t passed as void*, NULL = the legacy default stream) and
+ *     runs asynchronously; buffers must stay valid until it completes.
+ *
+ * ERRORS: every call returns an arp_status; nothing aborts and no C++
+ *     exception crosses this boundary.  arp_last_error() gives a message for
+ *     the last failing call on a context.  A context whose call returned
+ *     ARP_ECUDA or ARP_ETIMEOUT should be destroyed.
+ *
+ * THREADS: a context may be used by one host thread at a time.
+ */
+#ifndef ARP_H
+#define ARP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct arp_ctx arp_ctx;
+
+typedef enum {
+  ARP_OK = 0,
+  ARP_EINVAL = 1,       /* invalid argument (size, pointer, option) */
+  ARP_ENOMEM = 2,       /* device allocation failed */
+  ARP_ECUDA = 3,        /* a CUDA call or kernel launch failed */
+  ARP_ETIMEOUT = 4,     /* a bounded wait inside a kernel gave up */
+  ARP_ENONFINITE = 5    /* a result contained NaN or Inf */
+} arp_status;
+
+typedef enum {
+  ARP_FP64 = 0,         /* all arithmetic in FP64 */
+  ARP_FP32 = 1          /* fine and coarse bulk arithmetic in FP32; tables and
+                           phases computed in FP64 and rounded; parareal
+                           correction and norm in FP64 */
+} arp_precision;
+
+typedef enum {
+  ARP_OPT_T0 = 1,          /* averaging window in fast-time units (default dT/eps) */
+  ARP_OPT_F = 2,           /* the free parameter F of Eq. 6.1 (default 1) */
+  ARP_OPT_PRECISION = 3,   /* an arp_precision value (default ARP_FP64) */
+  ARP_OPT_KMAX = 4,        /* iteration cap used by arp_parareal_solve (default 5) */
+  ARP_OPT_TOL = 5          /* stopping tolerance of arp_parareal_solve (default 0) */
+} arp_option;
+
+/*
+ * arp_create: a context for one problem.
+ *   N      grid points, a power of two in [8, 2048]
+ *   eps    Rossby number (> 0; +inf switches the fast term off)
+ *   nu     hyperviscosity coefficient (>= 0), D_k = -nu k^4 (Sec. 6.1; the
+ *          printed +mu d^4/dx^4 is read as dissipation)
+ *   slices number of parareal time slices S >= 1 (Sec. 3)
+ *   dT     slice length (coarse step) > 0; the horizon is T = S dT
+ *   dt     fine step, 0 < dt <= dT; the fine propagator takes
+ *          steps = ceil(dT/dt - 1e-9) ETDRK4 steps of size dT/steps
+ *   M      quadrature points of the time average (Eq. 2.2, Algorithm 1), >= 2
+ * Computes every table on the device (synchronously) before returning.
+ * Returns ARP_EINVAL for invalid sizes, ARP_ENOMEM / ARP_ECUDA on failure;
+ * *out is NULL unless ARP_OK.
+ */
+arp_status arp_create(arp_ctx** out, int N, double eps, double nu, int slices,
+                      double dT, double dt, int M);
+
+/* arp_set_option: set an arp_option (tables are rebuilt on the next call that
+ * needs them).  ARP_EINVAL for an unknown key or an out-of-range value. */
+arp_status arp_set_option(arp_ctx* ctx, int key, double value);
+
+/* arp_query_bytes: device bytes a context with these sizes allocates (for
+ * admission control); 0 for invalid sizes. */
+size_t arp_query_bytes(int N, int slices, int M, int precision);
+
+/*
+ * arp_fine_batch: the fine propagator phi_dT (Sec. 3) applied to `batch`
+ * independent states, U_out[b] = F(U_in[b]): `steps` ETDRK4 steps (Cox &
+ * Matthews; the fine integrator named in Sec. 6.2) with the stiff linear part
+ * exp(h(-L/eps + D)) applied exactly per wavenumber through L's
+ * eigen-decomposition (Sec. 6.1) and N(u) formed pseudo-spectrally.
+ * U_in, U_out: device, [batch][3][H] complex doubles; may not overlap.
+ * batch = 0 is a no-op.  ARP_EINVAL for batch < 0 or NULL buffers.
+ */
+arp_status arp_fine_batch(arp_ctx* ctx, const double* U_in, double* U_out, int batch,
+                          void* stream);
+
+/*
+ * arp_coarse_avg: the discretised average of the nonlinearity (Eq. 2.1-2.2,
+ * Algorithm 1) for `batch` states:
+ *   Nbar(u) = sum_{m=0}^{M-1} w_m e^{s_m L} N(e^{-s_m L} u),
+ *   s_m = T0 m / M (fast time), w_m = rho(m/M)/M, rho(s) = C e^{-1/(s(1-s))}
+ *   on (0,1) with int_0^1 rho = 1 (Sec. 2).
+ * U_in, Nbar_out: device, [batch][3][H] complex doubles; may not overlap.
+ * The sum over m is reduced on chip in a fixed order (results do not depend
+ * on batch).  batch = 0 is a no-op.
+ */
+arp_status arp_coarse_avg(arp_ctx* ctx, const double* U_in, double* Nbar_out, int batch,
+                          void* stream);
+
+/*
+ * arp_coarse_step: the asymptotic slow solver over dT (Algorithm 2) for
+ * `batch` states:  w = e^{dT/2 D} u; k1 = Nbar(w); k2 = Nbar(w + dT/2 k1);
+ * w = e^{dT/2 D}(w + dT k2); G(u) = e^{-(dT/eps) L} w  (the map back to fast
+ * time of Sec. 3; the printed e^{+(dT/eps) L} is read as this).
+ * Layout as arp_fine_batch.
+ */
+arp_status arp_coarse_step(arp_ctx* ctx, const double* U_in, double* U_out, int batch,
+                           void* stream);
+
+/* arp_set_initial: u0 for the parareal iteration, one state [3][H].  u0 may be
+ * a host or a device pointer.  Resets the iteration (the next
+ * arp_parareal_iterate is the coarse predictor). */
+arp_status arp_set_initial(arp_ctx* ctx, const double* u0, void* stream);
+
+/*
+ * arp_parareal_iterate: one parareal iteration (Eq. 3.1, Algorithm 4).
+ * The first call after arp_set_initial is the coarse predictor
+ * U_n^0 = G(U_{n-1}^0), n = 1..S, and reports *max_rel_change = +inf.
+ * Each later call k >= 1 computes, in this order: F(U_n^{k-1}) for all
+ * n < S in parallel; V_n = F(U_n^{k-1}) - G(U_n^{k-1}) (FP64);
+ * the serial chain U_{n+1}^k = G(U_n^k) + V_n with U_0^k = u0; and
+ * *max_rel_change = max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k|| (L2 over the
+ * three fields via Parseval).  Synchronises `stream` to read the norm back.
+ * *k_done receives the iteration level just completed.
+ * ARP_EINVAL if no initial state was set; ARP_ENONFINITE if the change is
+ * NaN or Inf (the iterate is kept).
+ */
+arp_status arp_parareal_iterate(arp_ctx* ctx, void* stream, int* k_done,
+                                double* max_rel_change);
+
+/* arp_parareal_solve: arp_parareal_iterate until k = KMAX or the change is
+ * <= TOL (options), starting from the current level. */
+arp_status arp_parareal_solve(arp_ctx* ctx, void* stream, int* k_done, double* max_rel_change);
+
+/* arp_get_slices: copy the current iterate U_0..U_S, [(S+1)][3][H] complex
+ * doubles, to U (host or device pointer).  Synchronises `stream` when U is a
+ * host pointer. */
+arp_status arp_get_slices(arp_ctx* ctx, double* U, void* stream);
+
+/* arp_destroy: release the context and everything it owns (NULL is allowed). */
+arp_status arp_destroy(arp_ctx* ctx);
+
+/* arp_last_error: message of the last failed call on ctx (or of the last failed
+ * arp_create when ctx is NULL); never NULL; valid until the next call. */
+const char* arp_last_error(const arp_ctx* ctx);
+
+/* arp_info: sizes of a context: out[0]=N, out[1]=H, out[2]=K, out[3]=slices,
+ * out[4]=M, out[5]=fine steps per slice, out[6]=current level k (-1 before the
+ * predictor), out[7]=precision. */
+arp_status arp_info(const arp_ctx* ctx, int* out8);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARP_H */

@@ -1,0 +1,215 @@
+"""ctypes binding of libarp.so (include/arp.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+plain pointers and sizes through; all computation runs in the library's CUDA
+kernels.  Tensors are torch complex128 tensors of shape (batch, 3, N/2+1)
+(device tensors unless a function accepts host memory); the stream defaults to
+torch's current CUDA stream.  There is no CPU fallback: if the library cannot
+be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libarp.so")
+
+ARP_OK, ARP_EINVAL, ARP_ENOMEM, ARP_ECUDA, ARP_ETIMEOUT, ARP_ENONFINITE = range(6)
+ARP_FP64, ARP_FP32 = 0, 1
+ARP_OPT_T0, ARP_OPT_F, ARP_OPT_PRECISION, ARP_OPT_KMAX, ARP_OPT_TOL = 1, 2, 3, 4, 5
+STATUS_NAMES = {0: "ARP_OK", 1: "ARP_EINVAL", 2: "ARP_ENOMEM", 3: "ARP_ECUDA", 4: "ARP_ETIMEOUT",
+                5: "ARP_ENONFINITE"}
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "arp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+    "arp_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "arp_query_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "arp_fine_batch": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "arp_coarse_avg": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "arp_coarse_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "arp_set_initial": (ctypes.c_int, [_P, _P, _P]),
+    "arp_parareal_iterate": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "arp_parareal_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "arp_get_slices": (ctypes.c_int, [_P, _P, _P]),
+    "arp_destroy": (ctypes.c_int, [_P]),
+    "arp_last_error": (ctypes.c_char_p, [_P]),
+    "arp_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+class ArpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libarp.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run `python -m paper_1303_6615_gb300.build`)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _stream(stream) -> int:
+    if stream is not None:
+        return int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check(ctx, status: int):
+    if status != ARP_OK:
+        msg = load_library().arp_last_error(ctx)
+        raise ArpError(status, msg.decode() if msg else "")
+
+
+def _states(t, name: str, H: int):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a complex128 tensor")
+    if t.dim() != 3 or t.shape[1] != 3 or t.shape[2] != H or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (batch, 3, {H}) tensor")
+    return t.shape[0]
+
+
+def arp_create(N: int, eps: float, nu: float, slices: int, dT: float, dt: float, M: int) -> int:
+    lib = load_library()
+    h = _P()
+    st = lib.arp_create(ctypes.byref(h), N, eps, nu, slices, dT, dt, M)
+    _check(None, st)
+    return h.value
+
+
+def arp_set_option(ctx: int, key: int, value: float) -> None:
+    _check(ctx, load_library().arp_set_option(ctx, key, float(value)))
+
+
+def arp_query_bytes(N: int, slices: int, M: int, precision: int) -> int:
+    return load_library().arp_query_bytes(N, slices, M, precision)
+
+
+def arp_info(ctx: int) -> dict:
+    out = (ctypes.c_int * 8)()
+    _check(ctx, load_library().arp_info(ctx, out))
+    keys = ("N", "H", "K", "slices", "M", "steps", "level", "precision")
+    return dict(zip(keys, list(out)))
+
+
+def _batch_call(fn_name: str, ctx: int, U_in, U_out, stream=None) -> None:
+    H = arp_info(ctx)["H"]
+    b = _states(U_in, "U_in", H)
+    b2 = _states(U_out, "U_out", H)
+    if b != b2:
+        raise ValueError("U_in and U_out batch sizes differ")
+    if b and (not U_in.is_cuda or not U_out.is_cuda):
+        raise ValueError("U_in and U_out must be device tensors")
+    fn = getattr(load_library(), fn_name)
+    _check(ctx, fn(ctx, U_in.data_ptr() or None, U_out.data_ptr() or None, int(b), _stream(stream)))
+
+
+def arp_fine_batch(ctx: int, U_in, U_out, stream=None) -> None:
+    _batch_call("arp_fine_batch", ctx, U_in, U_out, stream)
+
+
+def arp_coarse_avg(ctx: int, U_in, Nbar_out, stream=None) -> None:
+    _batch_call("arp_coarse_avg", ctx, U_in, Nbar_out, stream)
+
+
+def arp_coarse_step(ctx: int, U_in, U_out, stream=None) -> None:
+    _batch_call("arp_coarse_step", ctx, U_in, U_out, stream)
+
+
+def arp_set_initial(ctx: int, u0, stream=None) -> None:
+    """u0: complex128 tensor (3, H) or (1, 3, H), host or device."""
+    H = arp_info(ctx)["H"]
+    t = u0.reshape(1, 3, H) if u0.dim() == 2 else u0
+    _states(t, "u0", H)
+    _check(ctx, load_library().arp_set_initial(ctx, t.data_ptr(), _stream(stream)))
+
+
+def arp_parareal_iterate(ctx: int, stream=None) -> tuple[int, float]:
+    k = ctypes.c_int(0)
+    ch = ctypes.c_double(0.0)
+    _check(ctx, load_library().arp_parareal_iterate(ctx, _stream(stream), ctypes.byref(k), ctypes.byref(ch)))
+    return k.value, ch.value
+
+
+def arp_parareal_solve(ctx: int, stream=None) -> tuple[int, float]:
+    k = ctypes.c_int(0)
+    ch = ctypes.c_double(0.0)
+    _check(ctx, load_library().arp_parareal_solve(ctx, _stream(stream), ctypes.byref(k), ctypes.byref(ch)))
+    return k.value, ch.value
+
+
+def arp_get_slices(ctx: int, U, stream=None) -> None:
+    """U: complex128 tensor (slices+1, 3, H), host or device."""
+    info = arp_info(ctx)
+    b = _states(U, "U", info["H"])
+    if b != info["slices"] + 1:
+        raise ValueError("U must hold slices+1 states")
+    _check(ctx, load_library().arp_get_slices(ctx, U.data_ptr(), _stream(stream)))
+
+
+def arp_destroy(ctx: int) -> None:
+    if ctx:
+        _check(None, load_library().arp_destroy(ctx))
+
+
+def arp_last_error(ctx: Optional[int]) -> str:
+    msg = load_library().arp_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+class Solver:
+    """Owning wrapper around one context (closes it on `close()` / exit)."""
+
+    def __init__(self, N: int, eps: float, nu: float, slices: int, dT: float, dt: float, M: int,
+                 precision: int = ARP_FP64, T0: Optional[float] = None, F: Optional[float] = None):
+        self.ctx = arp_create(N, eps, nu, slices, dT, dt, M)
+        try:
+            if precision != ARP_FP64:
+                arp_set_option(self.ctx, ARP_OPT_PRECISION, precision)
+            if T0 is not None:
+                arp_set_option(self.ctx, ARP_OPT_T0, T0)
+            if F is not None:
+                arp_set_option(self.ctx, ARP_OPT_F, F)
+        except Exception:
+            arp_destroy(self.ctx)
+            raise
+        self.info = arp_info(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            arp_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,90 @@
+// context.h -- host-side context of the asymptotic parareal library and the
+// internal launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "arp.h"
+#include "common.cuh"
+
+struct arp_ctx {
+  // problem
+  int N = 0, logN = 0, H = 0, K = 0, K1 = 0;
+  int slices = 0, M = 0, steps = 0, P = 0;  // P = quadrature chunks = ceil(M / kQuadChunk)
+  double eps = 0, nu = 0, dT = 0, dt = 0, h = 0;
+  double T0 = 0, F = 1.0, tol = 0.0;
+  bool T0_set = false;
+  int kmax = 5;
+  int precision = ARP_FP64;
+  int device = 0;
+  bool tables_dirty = true;
+
+  // FP64 tables (always), FP32 copies (rounded from FP64)
+  double* inv_sig64 = nullptr;   // [K1]
+  double* sk_sig64 = nullptr;    // [K1]
+  float* inv_sig32 = nullptr;
+  float* sk_sig32 = nullptr;
+  arp::cd* etd64 = nullptr;      // [6][3][K1]: E, E2, Q, f1, f2x2, f3
+  arp::cf* etd32 = nullptr;
+  arp::cd* tw64 = nullptr;       // [N/2] e^{-2 pi i t/N}
+  arp::cf* tw32 = nullptr;
+  arp::cd* phase64 = nullptr;    // [M][3][K1] e^{-i omega s_m}
+  arp::cf* phase32 = nullptr;
+  double* weight64 = nullptr;    // [M] w_m
+  float* weight32 = nullptr;
+  double* dhalf = nullptr;       // [K1] e^{-nu k^4 dT/2}
+  arp::cd* gphase = nullptr;     // [3][K1] e^{-i omega dT/eps}
+
+  // workspaces (sized for `slices` states)
+  arp::cd* W = nullptr;          // [slices][3][K1] eigen, FP64
+  arp::cd* W2 = nullptr;         // [slices][3][K1]
+  arp::cd* partial = nullptr;    // [slices][P][3][K1]
+  double* rel = nullptr;         // [slices + 1] per-slice relative change
+  double* scalar = nullptr;      // [2]: max relative change, status bits
+
+  // parareal state, physical spectral FP64, [(slices+1)][3][H] each
+  arp::cd* U = nullptr;          // current iterate
+  arp::cd* Uold = nullptr;       // previous iterate
+  arp::cd* Gc = nullptr;         // G(U_n) of the current iterate, n < slices
+  arp::cd* Fb = nullptr;         // F(U_n), n < slices
+  arp::cd* V = nullptr;          // F - G
+  int level = -1;                // -1: no initial state; 0: predictor pending
+  bool have_initial = false;
+
+  std::string err;
+};
+
+namespace arp {
+
+// Stores a message and returns the status.
+arp_status fail(arp_ctx* c, arp_status s, const std::string& msg);
+arp_status check_cuda(arp_ctx* c, cudaError_t e, const char* what);
+
+// tables.cu
+arp_status build_tables(arp_ctx* c, cudaStream_t s);
+
+// fine.cu: F applied to `batch` physical states.
+arp_status launch_fine(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
+
+// coarse.cu
+//   to_eigen: W[b] = (dhalf if use_dhalf) * R^H u[b]
+arp_status launch_to_eigen(arp_ctx* c, const cd* u, cd* W, int batch, bool use_dhalf, cudaStream_t s);
+//   nbar_partial: partial[b][p] = sum over chunk p of w_m e^{i w s_m} b(R e^{-i w s_m} W[b])
+arp_status launch_nbar_partial(arp_ctx* c, const cd* W, cd* partial, int batch, cudaStream_t s);
+//   reduce epilogues (sum over chunks p in order, then):
+enum ReduceMode { kReduceAvg = 0, kReduceMid = 1, kReduceFinal = 2 };
+//   kReduceAvg:   out_phys[b] = R Nbar
+//   kReduceMid:   W2[b] = W[b] + dT/2 Nbar
+//   kReduceFinal: g = gphase * dhalf * (W[b] + dT Nbar); out_phys[b] = R g;
+//                 if out2: out2_phys[b] = R g (+ vadd[b] when vadd is given)
+arp_status launch_nbar_reduce(arp_ctx* c, int mode, const cd* partial, const cd* W, cd* W2,
+                              cd* out_phys, const cd* vadd, cd* out2_phys, int batch, cudaStream_t s);
+arp_status coarse_avg(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
+arp_status coarse_step(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
+
+// parareal.cu
+arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);
+
+}  // namespace arp

@@ -1,0 +1,218 @@
+// fine_impl.cuh -- the fine propagator F over one slice: `steps` ETDRK4 steps
+// (Cox & Matthews; the fine integrator named in Sec. 6.2) of
+//     da/dt = lambda a + R^H N(R a),  lambda = -i omega/eps - nu k^4,
+// in L's eigen coordinates a (Sec. 6.1), where the stiff linear part is exact:
+//     a1 = E2 u + Q N(u)
+//     a2 = E2 u + Q N(a1)
+//     a3 = E2 a1 + Q (2 N(a2) - N(u))
+//     u+ = E u + f1 N(u) + 2 f2 (N(a1) + N(a2)) + f3 N(a3).
+//
+// One CUDA block per state.  The state's mode arrays (u, N(u), a1 and the
+// running sum of the update) and the two FFT lanes stay in shared memory for
+// the whole sweep; only the input and output states touch global memory.
+// After each transform a single pass over wavenumbers unpacks N, applies the
+// ETDRK4 combination for the stage, and packs the next stage's input.
+#pragma once
+
+#include "context.h"
+#include "spectral.cuh"
+
+namespace arp {
+
+template <typename T> __device__ __forceinline__ cpx<T> ldgc(const cpx<T>* p);
+template <> __device__ __forceinline__ cd ldgc<double>(const cd* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+template <> __device__ __forceinline__ cf ldgc<float>(const cf* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+template <typename T>
+struct FineTabs {
+  EtdView<T> etd;
+  const cpx<T>* tw;
+  const T* is;
+  const T* ss;
+  const double* is64;
+  const double* ss64;
+};
+
+template <int LOGN> struct FineBlock {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int value = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
+};
+
+template <typename T>
+inline size_t fine_smem_bytes(int N) {
+  const int K1 = (N - 1) / 3 + 1;
+  return (size_t)(2 * N + N / 2 + 12 * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
+}
+
+// Reads state b of a physical FP64 buffer [batch][3][H] and returns its eigen
+// amplitudes at wavenumber k (k = 0 coefficients taken as real).
+__device__ __forceinline__ void load_eigen64(const cd* __restrict__ src, int H, int k, double is, double ss, cd a[3]) {
+  cd u[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    u[f] = src[f * H + k];
+    if (k == 0) u[f].y = 0.0;
+  }
+  phys_to_eigen<double>(u, is, ss, a);
+}
+
+// Writes eigen amplitudes a at wavenumber k as physical coefficients.
+__device__ __forceinline__ void store_phys64(cd* __restrict__ dst, int H, int k, double is, double ss, const cd a[3]) {
+  cd u[3];
+  eigen_to_phys<double>(a, is, ss, u);
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    if (k == 0) u[f].y = 0.0;
+    dst[f * H + k] = u[f];
+  }
+}
+
+template <typename T, int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict__ in, cd* __restrict__ out,
+                                                           int steps, FineTabs<T> tb) {
+  constexpr int N = 1 << LOGN;
+  constexpr int H = N / 2 + 1;
+  constexpr int K = (N - 1) / 3;
+  constexpr int K1 = K + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* Z0 = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* Z1 = Z0 + N;
+  cpx<T>* TW = Z1 + N;
+  cpx<T>* U = TW + N / 2;
+  cpx<T>* NU = U + 3 * K1;
+  cpx<T>* A1 = NU + 3 * K1;
+  cpx<T>* ACC = A1 + 3 * K1;
+  T* IS = reinterpret_cast<T*>(ACC + 3 * K1);
+  T* SS = IS + K1;
+
+  const cd* src = in + (size_t)blockIdx.x * 3 * H;
+  for (int t = threadIdx.x; t < N / 2; t += BLOCK) TW[t] = tb.tw[t];
+  for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
+    if (k <= K) {
+      const T is = tb.is[k], ss = tb.ss[k];
+      IS[k] = is;
+      SS[k] = ss;
+      cd a[3];
+      load_eigen64(src, H, k, tb.is64[k], tb.ss64[k], a);
+      cpx<T> at[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        at[q] = cvt<T>(a[q]);
+        U[q * K1 + k] = at[q];
+      }
+      pack_mode<T, N>(Z0, Z1, k, at, is, ss);
+    } else {
+      zero_mode<T, N>(Z0, Z1, k);
+    }
+  }
+  __syncthreads();
+
+  const EtdView<T> e = tb.etd;
+#pragma unroll 1
+  for (int step = 0; step < steps; ++step) {
+    const bool last = (step == steps - 1);
+#pragma unroll 1
+    for (int stage = 0; stage < 4; ++stage) {
+      nonlinear_transform<T, LOGN, BLOCK>(Z0, Z1, TW);
+      const bool pack_next = !(last && stage == 3);
+      for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
+        if (k > K) {
+          if (pack_next) zero_mode<T, N>(Z0, Z1, k);
+          continue;
+        }
+        const T is = IS[k], ss = SS[k];
+        cpx<T> bn[3], nx[3];
+        unpack_mode<T, N>(Z0, Z1, k, is, ss, bn);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int i = q * K1 + k;
+          if (stage == 0) {
+            const cpx<T> u = U[i];
+            NU[i] = bn[q];
+            const cpx<T> a = ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn[q];
+            A1[i] = a;
+            ACC[i] = ldgc(e.E + i) * u + ldgc(e.f1 + i) * bn[q];
+            nx[q] = a;
+          } else if (stage == 1) {
+            ACC[i] = ACC[i] + ldgc(e.f2x2 + i) * bn[q];
+            nx[q] = ldgc(e.E2 + i) * U[i] + ldgc(e.Q + i) * bn[q];
+          } else if (stage == 2) {
+            ACC[i] = ACC[i] + ldgc(e.f2x2 + i) * bn[q];
+            nx[q] = ldgc(e.E2 + i) * A1[i] + ldgc(e.Q + i) * ((T)2 * bn[q] - NU[i]);
+          } else {
+            const cpx<T> u = ACC[i] + ldgc(e.f3 + i) * bn[q];
+            U[i] = u;
+            nx[q] = u;
+          }
+        }
+        if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
+      }
+      __syncthreads();
+    }
+  }
+
+  cd* dst = out + (size_t)blockIdx.x * 3 * H;
+  for (int k = threadIdx.x; k < H; k += BLOCK) {
+    if (k <= K) {
+      cd a[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) a[q] = cvt<double>(U[q * K1 + k]);
+      store_phys64(dst, H, k, tb.is64[k], tb.ss64[k], a);
+    } else {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) dst[f * H + k] = {0.0, 0.0};
+    }
+  }
+}
+
+template <typename T>
+FineTabs<T> fine_tabs(const arp_ctx* c);
+
+template <>
+inline FineTabs<double> fine_tabs<double>(const arp_ctx* c) {
+  const int n = 3 * c->K1;
+  return {{c->etd64, c->etd64 + n, c->etd64 + 2 * n, c->etd64 + 3 * n, c->etd64 + 4 * n, c->etd64 + 5 * n},
+          c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64};
+}
+
+template <>
+inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
+  const int n = 3 * c->K1;
+  return {{c->etd32, c->etd32 + n, c->etd32 + 2 * n, c->etd32 + 3 * n, c->etd32 + 4 * n, c->etd32 + 5 * n},
+          c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64};
+}
+
+template <typename T, int LOGN>
+arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
+  constexpr int BLOCK = FineBlock<LOGN>::value;
+  const size_t smem = fine_smem_bytes<T>(1 << LOGN);
+  auto kern = fine_sweep_kernel<T, LOGN, BLOCK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");
+  kern<<<batch, BLOCK, smem, s>>>(in, out, c->steps, fine_tabs<T>(c));
+  return check_cuda(c, cudaGetLastError(), "fine: launch");
+}
+
+template <typename T>
+arp_status launch_fine_prec(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
+  switch (c->logN) {
+    case 3: return launch_fine_n<T, 3>(c, in, out, batch, s);
+    case 4: return launch_fine_n<T, 4>(c, in, out, batch, s);
+    case 5: return launch_fine_n<T, 5>(c, in, out, batch, s);
+    case 6: return launch_fine_n<T, 6>(c, in, out, batch, s);
+    case 7: return launch_fine_n<T, 7>(c, in, out, batch, s);
+    case 8: return launch_fine_n<T, 8>(c, in, out, batch, s);
+    case 9: return launch_fine_n<T, 9>(c, in, out, batch, s);
+    case 10: return launch_fine_n<T, 10>(c, in, out, batch, s);
+    case 11: return launch_fine_n<T, 11>(c, in, out, batch, s);
+    default: return fail(c, ARP_EINVAL, "fine: unsupported grid size");
+  }
+}
+
+}  // namespace arp

@@ -1,0 +1,133 @@
+// parareal.cu -- one iteration of the parareal method (Eq. 3.1, Algorithm 4):
+//   U_0^k = u0,
+//   U_{n+1}^k = G(U_n^k) + F(U_n^{k-1}) - G(U_n^{k-1}),   k >= 1,
+// with the predictor U_{n+1}^0 = G(U_n^0).  F(U_n^{k-1}) for all slices runs
+// as one batched fine sweep; V_n = F - G is formed in FP64 in parallel; the
+// serial chain then evaluates G(U_n^k) slice after slice, keeping each value
+// as G(U_n^{k-1}) for the next iteration; finally the stopping quantity
+// max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k|| (L2 over the three fields by
+// Parseval: weight 1 at k = 0 and 2 above) is reduced in a fixed order.
+#include <cmath>
+
+#include "context.h"
+
+namespace arp {
+namespace {
+
+// V = F - G over n elements (complex FP64).
+__global__ void correction_kernel(const cd* __restrict__ f, const cd* __restrict__ g, cd* __restrict__ v, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = f[i] - g[i];
+}
+
+// One block (256 threads) per slice n = 1..S: rel[n] = ||U_n - Uold_n|| / ||U_n||.
+__global__ void slice_change_kernel(const cd* __restrict__ U, const cd* __restrict__ Uold, double* __restrict__ rel,
+                                    int H) {
+  __shared__ double sd[256], sn[256];
+  const int n = blockIdx.x + 1;
+  const size_t base = (size_t)n * 3 * H;
+  double d = 0.0, nn = 0.0;
+  for (int i = threadIdx.x; i < 3 * H; i += 256) {
+    const int k = i % H;
+    const double w = (k == 0) ? 1.0 : 2.0;
+    const cd a = U[base + i], b = Uold[base + i];
+    const double dx = a.x - b.x, dy = a.y - b.y;
+    d += w * (dx * dx + dy * dy);
+    nn += w * (a.x * a.x + a.y * a.y);
+  }
+  sd[threadIdx.x] = d;
+  sn[threadIdx.x] = nn;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sd[threadIdx.x] += sd[threadIdx.x + w];
+      sn[threadIdx.x] += sn[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double dd = sd[0], ns = sn[0];
+    double r;
+    if (ns > 0.0) r = sqrt(dd) / sqrt(ns);
+    else r = (dd > 0.0) ? INFINITY : 0.0;
+    rel[n] = r;
+  }
+}
+
+// One block: out[0] = max_n rel[n] (NaN if any entry is NaN).
+__global__ void max_kernel(const double* __restrict__ rel, int S, double* __restrict__ out) {
+  __shared__ double sm[256];
+  __shared__ int bad[256];
+  double m = 0.0;
+  int nan = 0;
+  for (int n = 1 + threadIdx.x; n <= S; n += 256) {
+    const double r = rel[n];
+    if (r != r) nan = 1;
+    else m = fmax(m, r);
+  }
+  sm[threadIdx.x] = m;
+  bad[threadIdx.x] = nan;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+      bad[threadIdx.x] |= bad[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = bad[0] ? NAN : sm[0];
+}
+
+// G(U_n) for the single state at U + n, written to g_out; u_next = g (+ v).
+arp_status chain_link(arp_ctx* c, const cd* u, cd* g_out, cd* u_next, const cd* v, cudaStream_t s) {
+  arp_status r;
+  if ((r = launch_to_eigen(c, u, c->W, 1, true, s)) != ARP_OK) return r;
+  if ((r = launch_nbar_partial(c, c->W, c->partial, 1, s)) != ARP_OK) return r;
+  if ((r = launch_nbar_reduce(c, kReduceMid, c->partial, c->W, c->W2, nullptr, nullptr, nullptr, 1, s)) != ARP_OK)
+    return r;
+  if ((r = launch_nbar_partial(c, c->W2, c->partial, 1, s)) != ARP_OK) return r;
+  return launch_nbar_reduce(c, kReduceFinal, c->partial, c->W, nullptr, g_out, v, u_next, 1, s);
+}
+
+}  // namespace
+
+arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change) {
+  const size_t st = (size_t)3 * c->H;  // complex entries per state
+  const int S = c->slices;
+  arp_status r;
+  if (c->level < 0) {
+    // predictor: U_{n+1} = G(U_n), G cached
+    for (int n = 0; n < S; ++n)
+      if ((r = chain_link(c, c->U + n * st, c->Gc + n * st, c->U + (n + 1) * st, nullptr, s)) != ARP_OK) return r;
+    c->level = 0;
+    if (k_done) *k_done = 0;
+    if (change) *change = INFINITY;
+    return ARP_OK;
+  }
+  std::swap(c->U, c->Uold);
+  if ((r = launch_fine(c, c->Uold, c->Fb, S, s)) != ARP_OK) return r;
+  const size_t nv = (size_t)S * st;
+  correction_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(c->Fb, c->Gc, c->V, nv);
+  if ((r = check_cuda(c, cudaGetLastError(), "correction: launch")) != ARP_OK) return r;
+  if ((r = check_cuda(c, cudaMemcpyAsync(c->U, c->Uold, st * sizeof(cd), cudaMemcpyDeviceToDevice, s),
+                      "copy u0")) != ARP_OK)
+    return r;
+  for (int n = 0; n < S; ++n)
+    if ((r = chain_link(c, c->U + n * st, c->Gc + n * st, c->U + (n + 1) * st, c->V + n * st, s)) != ARP_OK)
+      return r;
+  slice_change_kernel<<<S, 256, 0, s>>>(c->U, c->Uold, c->rel, c->H);
+  max_kernel<<<1, 256, 0, s>>>(c->rel, S, c->scalar);
+  if ((r = check_cuda(c, cudaGetLastError(), "norm: launch")) != ARP_OK) return r;
+  double h = 0.0;
+  if ((r = check_cuda(c, cudaMemcpyAsync(&h, c->scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "norm: read")) !=
+      ARP_OK)
+    return r;
+  if ((r = check_cuda(c, cudaStreamSynchronize(s), "norm: synchronise")) != ARP_OK) return r;
+  c->level += 1;
+  if (k_done) *k_done = c->level;
+  if (change) *change = h;
+  if (!std::isfinite(h)) return fail(c, ARP_ENONFINITE, "parareal: relative change is not finite");
+  return ARP_OK;
+}
+
+}  // namespace arp
