@@ -25,8 +25,11 @@
  *
  * ERRORS: every call returns an arp_status; nothing aborts and no C++
  *     exception crosses this boundary.  arp_last_error() gives a message for
- *     the last failing call on a context.  A context whose call returned
- *     ARP_ECUDA or ARP_ETIMEOUT should be destroyed.
+ *     the last failing call on a context.  Waits inside kernels are bounded:
+ *     a wait that gives up makes the call return ARP_ETIMEOUT and leaves the
+ *     CUDA context usable, but the parareal iterate is then undefined until
+ *     the next arp_set_initial.  After ARP_ECUDA the context should be
+ *     destroyed.
  *
  * THREADS: a context may be used by one host thread at a time.
  */
@@ -62,7 +65,12 @@ typedef enum {
   ARP_OPT_F = 2,           /* the free parameter F of Eq. 6.1 (default 1) */
   ARP_OPT_PRECISION = 3,   /* an arp_precision value (default ARP_FP64) */
   ARP_OPT_KMAX = 4,        /* iteration cap used by arp_parareal_solve (default 5) */
-  ARP_OPT_TOL = 5          /* stopping tolerance of arp_parareal_solve (default 0) */
+  ARP_OPT_TOL = 5,         /* stopping tolerance of arp_parareal_solve (default 0) */
+  ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook: a non-zero value makes
+                                      block 0 of the next coarse-chain launch skip its first
+                                      grid-barrier arrival, so every block's bounded wait
+                                      gives up (after about 1 s) and the call returns
+                                      ARP_ETIMEOUT; cleared after that launch */
 } arp_option;
 
 /*

@@ -38,11 +38,12 @@ struct Sizes {
 
 Sizes sizes_of(int N, int slices, int M) {
   const size_t H = N / 2 + 1, K1 = (N - 1) / 3 + 1, S = slices;
-  const size_t P = (M + kQuadChunk - 1) / kQuadChunk;
+  const size_t qc = (M + kMaxNodeBlocks - 1) / kMaxNodeBlocks;
+  const size_t P = (M + qc - 1) / qc;
   Sizes z;
-  z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + (N / 2) * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
+  z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (N / 2) * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
              (size_t)M * 12 + K1 * 8 + 3 * K1 * 16;
-  z.work = 2 * S * 3 * K1 * 16 + S * P * 3 * K1 * 16 + (S + 1) * 8 + 16;
+  z.work = 2 * S * 3 * K1 * 16 + (S + 1) * P * 3 * K1 * 16 + (S + 1) * 8 + 16 + 16;
   z.state = 2 * (S + 1) * 3 * H * 16 + 3 * S * 3 * H * 16;
   return z;
 }
@@ -61,10 +62,10 @@ arp_status alloc(arp_ctx* c, P** p, size_t bytes) {
 }
 
 void release(arp_ctx* c) {
-  void* ptrs[] = {c->inv_sig64, c->sk_sig64, c->inv_sig32, c->sk_sig32, c->etd64,   c->etd32, c->tw64,
+  void* ptrs[] = {c->E_lo32, c->inv_sig64, c->sk_sig64, c->inv_sig32, c->sk_sig32, c->etd64,   c->etd32, c->tw64,
                   c->tw32,      c->phase64,  c->phase32,   c->weight64,  c->weight32, c->dhalf, c->gphase,
                   c->W,         c->W2,       c->partial,   c->rel,       c->scalar,   c->U,     c->Uold,
-                  c->Gc,        c->Fb,       c->V};
+                  c->Gc,        c->Fb,       c->V,         c->sync,     c->part2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -80,6 +81,7 @@ arp_status allocate(arp_ctx* c) {
   ARP_ALLOC(c->sk_sig32, K1 * 4);
   ARP_ALLOC(c->etd64, 18 * K1 * 16);
   ARP_ALLOC(c->etd32, 18 * K1 * 8);
+  ARP_ALLOC(c->E_lo32, 3 * K1 * 8);
   ARP_ALLOC(c->tw64, (N / 2) * 16);
   ARP_ALLOC(c->tw32, (N / 2) * 8);
   ARP_ALLOC(c->phase64, M * 3 * K1 * 16);
@@ -93,6 +95,8 @@ arp_status allocate(arp_ctx* c) {
   ARP_ALLOC(c->partial, S * P * 3 * K1 * 16);
   ARP_ALLOC(c->rel, (S + 1) * 8);
   ARP_ALLOC(c->scalar, 16);
+  ARP_ALLOC(c->sync, 16);
+  ARP_ALLOC(c->part2, P * 3 * K1 * 16);
   ARP_ALLOC(c->U, (S + 1) * 3 * H * 16);
   ARP_ALLOC(c->Uold, (S + 1) * 3 * H * 16);
   ARP_ALLOC(c->Gc, S * 3 * H * 16);
@@ -170,7 +174,8 @@ arp_status arp_create(arp_ctx** out, int N, double eps, double nu, int slices, d
   c->K1 = c->K + 1;
   c->slices = slices;
   c->M = M;
-  c->P = (M + kQuadChunk - 1) / kQuadChunk;
+  c->qc = (M + kMaxNodeBlocks - 1) / kMaxNodeBlocks;
+  c->P = (M + c->qc - 1) / c->qc;
   c->eps = eps;
   c->nu = nu;
   c->dT = dT;
@@ -223,6 +228,9 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
     case ARP_OPT_TOL:
       if (!(v >= 0.0)) return fail(c, ARP_EINVAL, "TOL must be >= 0");
       c->tol = v;
+      return ARP_OK;
+    case ARP_OPT_TEST_SKIP_ARRIVAL:
+      c->skip_arrival = (v != 0.0);
       return ARP_OK;
     default:
       return fail(c, ARP_EINVAL, "unknown option key");

@@ -37,14 +37,59 @@ template <typename To, typename Ti> __host__ __device__ __forceinline__ cpx<To> 
 using cd = cpx<double>;
 using cf = cpx<float>;
 
+#if defined(__CUDACC__)
+// Unevaluated float pair hi + lo (|lo| <= ulp(hi)/2): about 48 significant
+// bits from FP32 arithmetic, using the error-free transforms of Knuth
+// (two-sum), Dekker (fast two-sum) and the FMA product error.
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// (a_hi + a_lo) + b
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  df s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+// (a_hi + a_lo) * (b_hi + b_lo) - (c_hi + c_lo) * (d_hi + d_lo)
+__device__ __forceinline__ df df_mul_sub(df a, df b, df c, df d) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const float q = __fmul_rn(c.hi, d.hi);
+  float f = __fmaf_rn(c.hi, d.hi, -q);
+  f = __fmaf_rn(c.hi, d.lo, __fmaf_rn(c.lo, d.hi, f));
+  df s = two_sum(p, -q);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(e, f)));
+}
+// complex pair arithmetic: z = (re, im) with each part a df
+struct cdf {
+  df re, im;
+};
+// (E_hi + E_lo) * (u_hi + u_lo), complex
+__device__ __forceinline__ cdf cdf_mul(cf eh, cf el, cf uh, cf ul) {
+  const df er{eh.x, el.x}, ei{eh.y, el.y}, ur{uh.x, ul.x}, ui{uh.y, ul.y};
+  const df nei{-ei.hi, -ei.lo};
+  return {df_mul_sub(er, ur, ei, ui), df_mul_sub(er, ui, nei, ur)};
+}
+__device__ __forceinline__ cdf cdf_add(cdf a, cf b) { return {df_add_f(a.re, b.x), df_add_f(a.im, b.y)}; }
+#endif
+
 // Eigen-branch index a = 0, 1, 2 stands for alpha = -1, 0, +1 (omega = alpha * sigma_k).
 constexpr int kBranches = 3;
 
-// Fixed quadrature-chunk size of the time average: one CUDA block evaluates the
-// nonlinearity at this many consecutive nodes s_m and sums them in order; the
-// chunk sums are then added in chunk order.  Fixed so that results do not
-// depend on the batch size.
-constexpr int kQuadChunk = 2;
+// The time average splits its M nodes into chunks of ceil(M / kMaxNodeBlocks)
+// consecutive nodes, one CUDA block per chunk; kMaxNodeBlocks is the SM count
+// of a GB300, so the persistent chain kernel keeps one block per SM.
+constexpr int kMaxNodeBlocks = 152;
 
 // Per-wavenumber constants of L's eigenvectors (Sec. 6.1), sigma_k = sqrt(1 + k^2/F):
 //   inv_sig[k] = 1/sigma_k, sk_sig[k] = F^-1/2 k / sigma_k.

@@ -12,7 +12,8 @@
 struct arp_ctx {
   // problem
   int N = 0, logN = 0, H = 0, K = 0, K1 = 0;
-  int slices = 0, M = 0, steps = 0, P = 0;  // P = quadrature chunks = ceil(M / kQuadChunk)
+  int slices = 0, M = 0, steps = 0;
+  int qc = 1, P = 0;             // nodes per block, node chunks P = ceil(M / qc)
   double eps = 0, nu = 0, dT = 0, dt = 0, h = 0;
   double T0 = 0, F = 1.0, tol = 0.0;
   bool T0_set = false;
@@ -28,6 +29,7 @@ struct arp_ctx {
   float* sk_sig32 = nullptr;
   arp::cd* etd64 = nullptr;      // [6][3][K1]: E, E2, Q, f1, f2x2, f3
   arp::cf* etd32 = nullptr;
+  arp::cf* E_lo32 = nullptr;     // [3][K1]: E - (double)(float)E, rounded to float
   arp::cd* tw64 = nullptr;       // [N/2] e^{-2 pi i t/N}
   arp::cf* tw32 = nullptr;
   arp::cd* phase64 = nullptr;    // [M][3][K1] e^{-i omega s_m}
@@ -42,7 +44,9 @@ struct arp_ctx {
   arp::cd* W2 = nullptr;         // [slices][3][K1]
   arp::cd* partial = nullptr;    // [slices][P][3][K1]
   double* rel = nullptr;         // [slices + 1] per-slice relative change
-  double* scalar = nullptr;      // [2]: max relative change, status bits
+  double* scalar = nullptr;      // [2]: max relative change
+  unsigned* sync = nullptr;      // [4]: [0] grid-barrier counter, [1] status (0 ok, else an arp_status)
+  arp::cd* part2 = nullptr;      // [P][3][K1] second partial buffer of the chain
 
   // parareal state, physical spectral FP64, [(slices+1)][3][H] each
   arp::cd* U = nullptr;          // current iterate
@@ -50,6 +54,7 @@ struct arp_ctx {
   arp::cd* Gc = nullptr;         // G(U_n) of the current iterate, n < slices
   arp::cd* Fb = nullptr;         // F(U_n), n < slices
   arp::cd* V = nullptr;          // F - G
+  int skip_arrival = 0;          // one-shot failure-detection test hook
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;
 
@@ -83,6 +88,11 @@ arp_status launch_nbar_reduce(arp_ctx* c, int mode, const cd* partial, const cd*
                               cd* out_phys, const cd* vadd, cd* out2_phys, int batch, cudaStream_t s);
 arp_status coarse_avg(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
 arp_status coarse_step(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
+
+// chain: the serial coarse chain U_{n+1} = G(U_n) (+ V_n), n = 0..S-1, one
+// cooperative persistent launch; Gc_n = G(U_n).  Returns ARP_EINVAL (without
+// launching) if the grid cannot be co-resident.
+arp_status launch_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
 
 // parareal.cu
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);

@@ -12,7 +12,15 @@
 // the whole sweep; only the input and output states touch global memory.
 // After each transform a single pass over wavenumbers unpacks N, applies the
 // ETDRK4 combination for the stage, and packs the next stage's input.
+//
+// FP32 path: transforms, products, stage values a1..a3 and the N(.) terms are
+// FP32, but the state u and the running update sum are carried as float pairs
+// hi + lo and multiplied by E = e^{h lambda} held as a float pair too, so the
+// exact linear propagation (a pure phase and decay per mode) does not pick up
+// a rounding error every step.  Only the N-evaluation input uses u_hi.
 #pragma once
+
+#include <type_traits>
 
 #include "context.h"
 #include "spectral.cuh"
@@ -32,6 +40,7 @@ template <> __device__ __forceinline__ cf ldgc<float>(const cf* p) {
 template <typename T>
 struct FineTabs {
   EtdView<T> etd;
+  const cf* E_lo;  // FP32 path: low part of E, [3][K1]
   const cpx<T>* tw;
   const T* is;
   const T* ss;
@@ -45,9 +54,14 @@ template <int LOGN> struct FineBlock {
 };
 
 template <typename T>
+constexpr int fine_mode_arrays() {
+  return std::is_same<T, float>::value ? 6 : 4;  // u, N(u), a1, acc (+ u_lo, acc_lo)
+}
+
+template <typename T>
 inline size_t fine_smem_bytes(int N) {
   const int K1 = (N - 1) / 3 + 1;
-  return (size_t)(2 * N + N / 2 + 12 * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
+  return (size_t)(2 * N + N / 2 + 3 * fine_mode_arrays<T>() * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
 }
 
 // Reads state b of a physical FP64 buffer [batch][3][H] and returns its eigen
@@ -88,7 +102,10 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
   cpx<T>* NU = U + 3 * K1;
   cpx<T>* A1 = NU + 3 * K1;
   cpx<T>* ACC = A1 + 3 * K1;
-  T* IS = reinterpret_cast<T*>(ACC + 3 * K1);
+  constexpr bool kPair = std::is_same<T, float>::value;
+  cpx<T>* ULO = ACC + 3 * K1;                       // FP32 path only
+  cpx<T>* ACCLO = ULO + (kPair ? 3 * K1 : 0);       // FP32 path only
+  T* IS = reinterpret_cast<T*>(ACC + 3 * K1 + (kPair ? 6 * K1 : 0));
   T* SS = IS + K1;
 
   const cd* src = in + (size_t)blockIdx.x * 3 * H;
@@ -105,6 +122,7 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
       for (int q = 0; q < 3; ++q) {
         at[q] = cvt<T>(a[q]);
         U[q * K1 + k] = at[q];
+        if constexpr (kPair) ULO[q * K1 + k] = cvt<float>(a[q] - cvt<double>(at[q]));
       }
       pack_mode<T, N>(Z0, Z1, k, at, is, ss);
     } else {
@@ -132,23 +150,51 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int i = q * K1 + k;
-          if (stage == 0) {
-            const cpx<T> u = U[i];
-            NU[i] = bn[q];
-            const cpx<T> a = ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn[q];
-            A1[i] = a;
-            ACC[i] = ldgc(e.E + i) * u + ldgc(e.f1 + i) * bn[q];
-            nx[q] = a;
-          } else if (stage == 1) {
-            ACC[i] = ACC[i] + ldgc(e.f2x2 + i) * bn[q];
-            nx[q] = ldgc(e.E2 + i) * U[i] + ldgc(e.Q + i) * bn[q];
-          } else if (stage == 2) {
-            ACC[i] = ACC[i] + ldgc(e.f2x2 + i) * bn[q];
-            nx[q] = ldgc(e.E2 + i) * A1[i] + ldgc(e.Q + i) * ((T)2 * bn[q] - NU[i]);
+          if constexpr (kPair) {
+            if (stage == 0) {
+              const cf u = U[i];
+              NU[i] = bn[q];
+              const cf a = ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn[q];
+              A1[i] = a;
+              const cdf acc = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(tb.E_lo + i), u, ULO[i]), ldgc(e.f1 + i) * bn[q]);
+              ACC[i] = mk<float>(acc.re.hi, acc.im.hi);
+              ACCLO[i] = mk<float>(acc.re.lo, acc.im.lo);
+              nx[q] = a;
+            } else if (stage == 3) {
+              const cf t = ldgc(e.f3 + i) * bn[q];
+              const cf ah = ACC[i], al = ACCLO[i];
+              const df re = df_add_f(df{ah.x, al.x}, t.x), im = df_add_f(df{ah.y, al.y}, t.y);
+              U[i] = mk<float>(re.hi, im.hi);
+              ULO[i] = mk<float>(re.lo, im.lo);
+              nx[q] = U[i];
+            } else {
+              const cf t = ldgc(e.f2x2 + i) * bn[q];
+              const cf ah = ACC[i], al = ACCLO[i];
+              const df re = df_add_f(df{ah.x, al.x}, t.x), im = df_add_f(df{ah.y, al.y}, t.y);
+              ACC[i] = mk<float>(re.hi, im.hi);
+              ACCLO[i] = mk<float>(re.lo, im.lo);
+              nx[q] = (stage == 1) ? ldgc(e.E2 + i) * U[i] + ldgc(e.Q + i) * bn[q]
+                                   : ldgc(e.E2 + i) * A1[i] + ldgc(e.Q + i) * ((T)2 * bn[q] - NU[i]);
+            }
           } else {
-            const cpx<T> u = ACC[i] + ldgc(e.f3 + i) * bn[q];
-            U[i] = u;
-            nx[q] = u;
+            if (stage == 0) {
+              const cpx<T> u = U[i];
+              NU[i] = bn[q];
+              const cpx<T> a = ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn[q];
+              A1[i] = a;
+              ACC[i] = ldgc(e.E + i) * u + ldgc(e.f1 + i) * bn[q];
+              nx[q] = a;
+            } else if (stage == 1) {
+              ACC[i] = ACC[i] + ldgc(e.f2x2 + i) * bn[q];
+              nx[q] = ldgc(e.E2 + i) * U[i] + ldgc(e.Q + i) * bn[q];
+            } else if (stage == 2) {
+              ACC[i] = ACC[i] + ldgc(e.f2x2 + i) * bn[q];
+              nx[q] = ldgc(e.E2 + i) * A1[i] + ldgc(e.Q + i) * ((T)2 * bn[q] - NU[i]);
+            } else {
+              const cpx<T> u = ACC[i] + ldgc(e.f3 + i) * bn[q];
+              U[i] = u;
+              nx[q] = u;
+            }
           }
         }
         if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
@@ -162,7 +208,10 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
     if (k <= K) {
       cd a[3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) a[q] = cvt<double>(U[q * K1 + k]);
+      for (int q = 0; q < 3; ++q) {
+        a[q] = cvt<double>(U[q * K1 + k]);
+        if constexpr (kPair) a[q] = a[q] + cvt<double>(ULO[q * K1 + k]);
+      }
       store_phys64(dst, H, k, tb.is64[k], tb.ss64[k], a);
     } else {
 #pragma unroll
@@ -178,14 +227,14 @@ template <>
 inline FineTabs<double> fine_tabs<double>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd64, c->etd64 + n, c->etd64 + 2 * n, c->etd64 + 3 * n, c->etd64 + 4 * n, c->etd64 + 5 * n},
-          c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64};
+          nullptr, c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64};
 }
 
 template <>
 inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd32, c->etd32 + n, c->etd32 + 2 * n, c->etd32 + 3 * n, c->etd32 + 4 * n, c->etd32 + 5 * n},
-          c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64};
+          c->E_lo32, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64};
 }
 
 template <typename T, int LOGN>

@@ -78,7 +78,9 @@ __global__ void max_kernel(const double* __restrict__ rel, int S, double* __rest
   if (threadIdx.x == 0) out[0] = bad[0] ? NAN : sm[0];
 }
 
-// G(U_n) for the single state at U + n, written to g_out; u_next = g (+ v).
+// G(U_n) for the single state at U + n, written to g_out; u_next = g (+ v), with
+// one launch per step of the link (used when the persistent chain cannot be
+// co-resident).
 arp_status chain_link(arp_ctx* c, const cd* u, cd* g_out, cd* u_next, const cd* v, cudaStream_t s) {
   arp_status r;
   if ((r = launch_to_eigen(c, u, c->W, 1, true, s)) != ARP_OK) return r;
@@ -89,6 +91,25 @@ arp_status chain_link(arp_ctx* c, const cd* u, cd* g_out, cd* u_next, const cd* 
   return launch_nbar_reduce(c, kReduceFinal, c->partial, c->W, nullptr, g_out, v, u_next, 1, s);
 }
 
+// The whole serial chain n = 0..S-1: the persistent cooperative kernel, else
+// one link at a time.
+arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
+  const size_t st = (size_t)3 * c->H;
+  arp_status r = launch_chain(c, c->U, c->Gc, V, s);
+  if (r != ARP_EINVAL) return r;
+  for (int n = 0; n < c->slices; ++n)
+    if ((r = chain_link(c, c->U + n * st, c->Gc + n * st, c->U + (n + 1) * st, V ? V + n * st : nullptr, s)) !=
+        ARP_OK)
+      return r;
+  return ARP_OK;
+}
+
+// Reads the chain's status word; ARP_ETIMEOUT if a grid barrier gave up.
+arp_status chain_status(arp_ctx* c, unsigned status) {
+  if (status == 0u) return ARP_OK;
+  return fail(c, ARP_ETIMEOUT, "chain: a grid barrier timed out");
+}
+
 }  // namespace
 
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change) {
@@ -97,8 +118,13 @@ arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* cha
   arp_status r;
   if (c->level < 0) {
     // predictor: U_{n+1} = G(U_n), G cached
-    for (int n = 0; n < S; ++n)
-      if ((r = chain_link(c, c->U + n * st, c->Gc + n * st, c->U + (n + 1) * st, nullptr, s)) != ARP_OK) return r;
+    if ((r = run_chain(c, nullptr, s)) != ARP_OK) return r;
+    unsigned status = 0;
+    if ((r = check_cuda(c, cudaMemcpyAsync(&status, c->sync + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                        "chain: status read")) != ARP_OK)
+      return r;
+    if ((r = check_cuda(c, cudaStreamSynchronize(s), "chain: synchronise")) != ARP_OK) return r;
+    if ((r = chain_status(c, status)) != ARP_OK) return r;
     c->level = 0;
     if (k_done) *k_done = 0;
     if (change) *change = INFINITY;
@@ -112,17 +138,26 @@ arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* cha
   if ((r = check_cuda(c, cudaMemcpyAsync(c->U, c->Uold, st * sizeof(cd), cudaMemcpyDeviceToDevice, s),
                       "copy u0")) != ARP_OK)
     return r;
-  for (int n = 0; n < S; ++n)
-    if ((r = chain_link(c, c->U + n * st, c->Gc + n * st, c->U + (n + 1) * st, c->V + n * st, s)) != ARP_OK)
-      return r;
+  if ((r = run_chain(c, c->V, s)) != ARP_OK) {
+    std::swap(c->U, c->Uold);
+    return r;
+  }
   slice_change_kernel<<<S, 256, 0, s>>>(c->U, c->Uold, c->rel, c->H);
   max_kernel<<<1, 256, 0, s>>>(c->rel, S, c->scalar);
   if ((r = check_cuda(c, cudaGetLastError(), "norm: launch")) != ARP_OK) return r;
   double h = 0.0;
+  unsigned status = 0;
   if ((r = check_cuda(c, cudaMemcpyAsync(&h, c->scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "norm: read")) !=
       ARP_OK)
     return r;
+  if ((r = check_cuda(c, cudaMemcpyAsync(&status, c->sync + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                      "chain: status read")) != ARP_OK)
+    return r;
   if ((r = check_cuda(c, cudaStreamSynchronize(s), "norm: synchronise")) != ARP_OK) return r;
+  if ((r = chain_status(c, status)) != ARP_OK) {
+    std::swap(c->U, c->Uold);
+    return r;
+  }
   c->level += 1;
   if (k_done) *k_done = c->level;
   if (change) *change = h;

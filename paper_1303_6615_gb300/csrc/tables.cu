@@ -89,7 +89,8 @@ __device__ __forceinline__ double omega_of(int b, int k, double s) {
 // One thread per wavenumber: branches alpha = 0 and +1 computed, alpha = -1 is
 // the conjugate of alpha = +1 (lambda_- = conj(lambda_+)), kept exact so that
 // real k = 0 fields stay real.
-__global__ void etd_kernel(int K1, double s, double inv_eps, double nu, double h, cd* etd64, cf* etd32) {
+__global__ void etd_kernel(int K1, double s, double inv_eps, double nu, double h, cd* etd64, cf* etd32,
+                           cf* elo32) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K1) return;
   const double k4 = (double)k * (double)k * (double)k * (double)k;
@@ -118,6 +119,11 @@ __global__ void etd_kernel(int K1, double s, double inv_eps, double nu, double h
         etd32[idm] = {(float)v[j].x, -(float)v[j].y};
       }
     }
+    // low parts of E for the FP32 path's float-pair propagation
+    const cf eh = {(float)v[0].x, (float)v[0].y};
+    const cf el = {(float)(v[0].x - (double)eh.x), (float)(v[0].y - (double)eh.y)};
+    elo32[b * K1 + k] = el;
+    if (b == 2) elo32[k] = {el.x, -el.y};
   }
 }
 
@@ -188,7 +194,7 @@ arp_status build_tables(arp_ctx* c, cudaStream_t st) {
   eigen_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->inv_sig64, c->sk_sig64, c->inv_sig32,
                                                            c->sk_sig32);
   twiddle_kernel<<<(c->N / 2 + tb - 1) / tb, tb, 0, st>>>(c->N, c->tw64, c->tw32);
-  etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32);
+  etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32);
   weights_kernel<<<1, 256, 0, st>>>(c->M, c->weight64, c->weight32);
   phase_kernel<<<dim3((c->K1 + tb - 1) / tb, c->M), tb, 0, st>>>(c->M, c->K1, s, T0, c->phase64, c->phase32);
   coarse_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->nu, c->dT, inv_eps, c->dhalf, c->gphase);

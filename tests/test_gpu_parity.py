@@ -268,3 +268,29 @@ def test_parareal_small_workload_fp32():
     ref = o.parareal(u0, p, w.slices, w.k_max)
     for k, (g, r) in enumerate(zip(its, ref.iterates)):
         assert per_state_rel_l2(g[1:], r[1:]).max() <= TOL32, k
+
+
+# ---------------------------------------------------------------- failure detection
+
+def test_chain_barrier_timeout_is_reported_and_context_stays_usable():
+    # Test hook: block 0 of the next chain launch skips its first barrier arrival,
+    # so every block's bounded wait gives up after about a second.
+    torch = cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    w = ri.SMALL_N64
+    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+    u0 = w.initial_state()
+    with _solver(p, w.slices) as s:
+        b.arp_set_initial(s.ctx, to_dev(u0))
+        b.arp_set_option(s.ctx, b.ARP_OPT_TEST_SKIP_ARRIVAL, 1)
+        with pytest.raises(b.ArpError) as ei:
+            b.arp_parareal_iterate(s.ctx)
+        assert ei.value.status == b.ARP_ETIMEOUT
+        # the CUDA context is intact: restart the iteration and compare with the oracle
+        b.arp_set_initial(s.ctx, to_dev(u0))
+        b.arp_parareal_iterate(s.ctx)
+        U = torch.empty((w.slices + 1, 3, p.H), dtype=torch.complex128, device="cuda")
+        b.arp_get_slices(s.ctx, U)
+        got = to_host(U)
+    ref = o.parareal(u0, p, w.slices, 0)
+    assert per_state_rel_l2(got[1:], ref.iterates[0][1:]).max() <= TOL64
