@@ -41,7 +41,7 @@ Sizes sizes_of(int N, int slices, int M) {
   const size_t qc = (M + kMaxNodeBlocks - 1) / kMaxNodeBlocks;
   const size_t P = (M + qc - 1) / qc;
   Sizes z;
-  z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (N / 2) * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
+  z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (size_t)N * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
              (size_t)M * 12 + K1 * 8 + 3 * K1 * 16;
   z.work = 2 * S * 3 * K1 * 16 + (S + 1) * P * 3 * K1 * 16 + (S + 1) * 8 + 16 + 16;
   z.state = 2 * (S + 1) * 3 * H * 16 + 3 * S * 3 * H * 16;
@@ -82,8 +82,8 @@ arp_status allocate(arp_ctx* c) {
   ARP_ALLOC(c->etd64, 18 * K1 * 16);
   ARP_ALLOC(c->etd32, 18 * K1 * 8);
   ARP_ALLOC(c->E_lo32, 3 * K1 * 8);
-  ARP_ALLOC(c->tw64, (N / 2) * 16);
-  ARP_ALLOC(c->tw32, (N / 2) * 8);
+  ARP_ALLOC(c->tw64, N * 16);
+  ARP_ALLOC(c->tw32, N * 8);
   ARP_ALLOC(c->phase64, M * 3 * K1 * 16);
   ARP_ALLOC(c->phase32, M * 3 * K1 * 8);
   ARP_ALLOC(c->weight64, M * 8);

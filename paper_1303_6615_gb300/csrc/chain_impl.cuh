@@ -7,11 +7,17 @@
 //     g = e^{-(dT/eps) L} e^{dT/2 D} (w + dT k2).
 //
 // One cooperative launch of P blocks (P = quadrature-node chunks, at most one
-// block per SM), persistent across all S links.  Block j evaluates the
-// nonlinearity at its nodes for both averages of a link and writes its partial
-// sum; a grid barrier separates the two averages and the links.  Every block
-// then sums the P partials in the same fixed order and so holds the same next
-// state without a third barrier; block 0 writes g_n and U_{n+1}.
+// block per SM), persistent across all S links.  Per link:
+//   A  every block evaluates the nonlinearity at its nodes for w and writes its
+//      partial sum;                                              -- barrier
+//   B  block j sums the P partials of its own wavenumbers (fixed order) and
+//      writes the midpoint state w + dT/2 k1 for them;           -- barrier
+//   C  every block reads the midpoint state, evaluates its nodes, writes the
+//      partial sum;                                              -- barrier
+//   D  block j sums those partials for its wavenumbers, forms g, U_{n+1} and the
+//      next link's w for them;                                   -- barrier
+// so the FP64 work of the epilogues (slow on this part) is spread over the
+// blocks instead of repeated in each.
 //
 // The grid barrier spins on a global counter with a wall-clock limit: after
 // kBarrierTimeoutNs a block records ARP_ETIMEOUT in the status word and every
@@ -32,10 +38,11 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 // Barrier across the co-resident blocks of a cooperative launch.  `epoch` is
 // the block's running target (gridDim.x per barrier); returns false if the
-// status word is set (a timeout here or elsewhere).
+// status word is set (a timeout here or elsewhere).  The block barrier orders
+// every thread's writes before thread 0's fence and arrival; thread 0's fence
+// after the wait orders the block's later reads.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* status, unsigned& epoch, bool arrive = true) {
   __shared__ int ok;
-  __threadfence();  // this thread's global writes before the block's arrival
   __syncthreads();
   if (threadIdx.x == 0) {
     epoch += gridDim.x;
@@ -55,7 +62,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* status, 
         good = 0;
         break;
       }
-      __nanosleep(64);
     }
     __threadfence();
     ok = good;
@@ -64,12 +70,19 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* status, 
   return ok != 0;
 }
 
+__device__ __forceinline__ cd ldcg_c(const cd* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+
 struct ChainArgs {
   const cd* V;       // [S][3][H] or null (predictor)
   cd* U;             // [(S+1)][3][H]; U_0 read, U_1..U_S written
   cd* Gc;            // [S][3][H] written
   cd* part1;         // [P][3][K1]
   cd* part2;         // [P][3][K1]
+  cd* wg;            // [3][K1] w of the current link (eigen, FP64)
+  cd* w2g;           // [3][K1] midpoint state
   unsigned* count;   // grid-barrier counter, zero at launch
   unsigned* status;  // zero at launch
   int S, M, chunk;
@@ -82,9 +95,34 @@ struct ChainArgs {
 };
 
 template <typename T>
-inline size_t chain_smem_bytes(int N) {
-  const int K1 = (N - 1) / 3 + 1;
-  return (size_t)(2 * N + N / 2 + 6 * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T) + (size_t)3 * K1 * sizeof(cd);
+inline size_t chain_smem_bytes(int logn) {
+  const int K1 = ((1 << logn) - 1) / 3 + 1;
+  return (size_t)(lanes_and_twiddles<T>(logn) + 6 * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
+}
+
+// Sums part[p][i] over p = 0..P-1 for the `count` indices i = first + r*stride...
+// Each sum is split over a half-warp (lane l takes p = l, l+16, ...) and closed
+// by a fixed shuffle tree, so the order of additions never changes.  Results go
+// to red[r] in shared memory (visible after the caller's __syncthreads()).
+template <int BLOCK>
+__device__ __forceinline__ void sum_partials(const cd* part, int P, int K1x3, const int* idx, int count, cd* red) {
+  const int lane = threadIdx.x & 15;
+  // the trip count is the same for every thread, so all lanes reach every shuffle
+  for (int it0 = 0; it0 < count; it0 += BLOCK / 16) {
+    const int it = it0 + (int)(threadIdx.x >> 4);
+    const bool active = it < count;
+    cd s = {0.0, 0.0};
+    if (active) {
+      const int i = idx[it];
+      for (int p = lane; p < P; p += 16) s = s + ldcg_c(part + (size_t)p * K1x3 + i);
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      s.x += __shfl_down_sync(0xffffffffu, s.x, off, 16);
+      s.y += __shfl_down_sync(0xffffffffu, s.y, off, 16);
+    }
+    if (active && lane == 0) red[it] = s;
+  }
 }
 
 template <typename T, int LOGN, int BLOCK>
@@ -93,25 +131,34 @@ __global__ void __launch_bounds__(BLOCK) chain_kernel(ChainArgs a, NbarTabs<T> t
   constexpr int H = N / 2 + 1;
   constexpr int K = (N - 1) / 3;
   constexpr int K1 = K + 1;
+  constexpr int kMaxOwn = 64;  // own wavenumbers per block (K1 <= 683 and P >= 11 for N = 2048)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cd* W64 = reinterpret_cast<cd*>(smem_raw);               // w of the current link, eigen FP64
-  cpx<T>* Z0 = reinterpret_cast<cpx<T>*>(W64 + 3 * K1);
-  cpx<T>* Z1 = Z0 + N;
-  cpx<T>* TW = Z1 + N;
-  cpx<T>* WS = TW + N / 2;
+  cpx<T>* Z0 = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* Z1 = Z0 + padded_len<T>(N);
+  cpx<T>* TW = Z1 + padded_len<T>(N);
+  cpx<T>* WS = TW + twiddle_count(LOGN);
   cpx<T>* ACC = WS + 3 * K1;
   T* IS = reinterpret_cast<T*>(ACC + 3 * K1);
   T* SS = IS + K1;
+  __shared__ int own_idx[3 * kMaxOwn];
+  __shared__ cd red[3 * kMaxOwn];
 
   const int j = blockIdx.x, P = gridDim.x;
   const int m0 = min(a.M, j * a.chunk);
   const int m1 = min(a.M, m0 + a.chunk);
+  const int per = (K1 + P - 1) / P;
+  const int k0 = min(K1, j * per), k1 = min(K1, k0 + per);
+  const int nown = k1 - k0;  // own wavenumbers, <= kMaxOwn (checked on the host)
   unsigned epoch = 0;
 
-  for (int t = threadIdx.x; t < N / 2; t += BLOCK) TW[t] = tb.tw[t];
+  for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TW[t] = tb.tw[t];
   for (int k = threadIdx.x; k < K1; k += BLOCK) {
     IS[k] = tb.is[k];
     SS[k] = tb.ss[k];
+  }
+  for (int r = threadIdx.x; r < 3 * nown; r += BLOCK) own_idx[r] = (r / nown) * K1 + k0 + r % nown;
+  // initial w = e^{dT/2 D} R^H U_0 for the own wavenumbers
+  for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
     cd x[3], e[3];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
@@ -120,75 +167,67 @@ __global__ void __launch_bounds__(BLOCK) chain_kernel(ChainArgs a, NbarTabs<T> t
     }
     phys_to_eigen<double>(x, a.is64[k], a.ss64[k], e);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      W64[q * K1 + k] = a.dhalf[k] * e[q];
-      WS[q * K1 + k] = cvt<T>(W64[q * K1 + k]);
-    }
+    for (int q = 0; q < 3; ++q) a.wg[q * K1 + k] = a.dhalf[k] * e[q];
   }
+  if (!grid_barrier(a.count, a.status, epoch)) return;
+  for (int i = threadIdx.x; i < 3 * K1; i += BLOCK) WS[i] = cvt<T>(ldcg_c(a.wg + i));
   __syncthreads();
 
 #pragma unroll 1
   for (int n = 0; n < a.S; ++n) {
-    // first average, on w
+    // A: first average, on w
     nbar_nodes<T, LOGN, BLOCK>(WS, ACC, m0, m1, tb, Z0, Z1, TW, IS, SS);
     for (int i = threadIdx.x; i < 3 * K1; i += BLOCK) a.part1[(size_t)j * 3 * K1 + i] = cvt<double>(ACC[i]);
     if (!grid_barrier(a.count, a.status, epoch, !(a.skip_arrival && j == 0 && n == 0))) return;
-    // midpoint state w + dT/2 k1, then the second average on it
-    for (int i = threadIdx.x; i < 3 * K1; i += BLOCK) {
-      cd s = {0.0, 0.0};
-      for (int p = 0; p < P; ++p) {
-        const double2 v = __ldcg(reinterpret_cast<const double2*>(a.part1 + (size_t)p * 3 * K1 + i));
-        s = s + cd{v.x, v.y};
-      }
-      WS[i] = cvt<T>(W64[i] + (0.5 * a.dT) * s);
+    // B: midpoint state w + dT/2 k1 for the own wavenumbers
+    sum_partials<BLOCK>(a.part1, P, 3 * K1, own_idx, 3 * nown, red);
+    __syncthreads();
+    for (int r = threadIdx.x; r < 3 * nown; r += BLOCK) {
+      const int i = own_idx[r];
+      a.w2g[i] = ldcg_c(a.wg + i) + (0.5 * a.dT) * red[r];
     }
+    if (!grid_barrier(a.count, a.status, epoch)) return;
+    // C: second average, on the midpoint state
+    for (int i = threadIdx.x; i < 3 * K1; i += BLOCK) WS[i] = cvt<T>(ldcg_c(a.w2g + i));
     __syncthreads();
     nbar_nodes<T, LOGN, BLOCK>(WS, ACC, m0, m1, tb, Z0, Z1, TW, IS, SS);
     for (int i = threadIdx.x; i < 3 * K1; i += BLOCK) a.part2[(size_t)j * 3 * K1 + i] = cvt<double>(ACC[i]);
     if (!grid_barrier(a.count, a.status, epoch)) return;
-    // g = e^{-(dT/eps)L} e^{dT/2 D}(w + dT k2); U_{n+1} = g + V_n; next w
+    // D: g = e^{-(dT/eps)L} e^{dT/2 D}(w + dT k2); U_{n+1} = g + V_n; next w
+    sum_partials<BLOCK>(a.part2, P, 3 * K1, own_idx, 3 * nown, red);
+    __syncthreads();
     cd* gout = a.Gc + (size_t)n * 3 * H;
     cd* uout = a.U + (size_t)(n + 1) * 3 * H;
     const cd* v = a.V ? a.V + (size_t)n * 3 * H : nullptr;
-    for (int k = threadIdx.x; k < H; k += BLOCK) {
-      if (k >= K1) {
-        if (j == 0) {
-#pragma unroll
-          for (int f = 0; f < 3; ++f) {
-            gout[f * H + k] = {0.0, 0.0};
-            uout[f * H + k] = {0.0, 0.0};
-          }
-        }
-        continue;
-      }
+    for (int r = threadIdx.x; r < nown; r += BLOCK) {
+      const int k = k0 + r;
       cd g[3], u[3], e[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int i = q * K1 + k;
-        cd s = {0.0, 0.0};
-        for (int p = 0; p < P; ++p) {
-          const double2 vv = __ldcg(reinterpret_cast<const double2*>(a.part2 + (size_t)p * 3 * K1 + i));
-          s = s + cd{vv.x, vv.y};
-        }
-        g[q] = a.dhalf[k] * (a.gphase[i] * (W64[i] + a.dT * s));
+        g[q] = a.dhalf[k] * (a.gphase[i] * (ldcg_c(a.wg + i) + a.dT * red[q * nown + r]));
       }
       eigen_to_phys<double>(g, a.is64[k], a.ss64[k], u);
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
         if (k == 0) u[f].y = 0.0;
-        if (j == 0) gout[f * H + k] = u[f];
+        gout[f * H + k] = u[f];
         if (v) u[f] = u[f] + v[f * H + k];
-        if (j == 0) uout[f * H + k] = u[f];
-        if (k == 0) u[f].y = 0.0;
+        uout[f * H + k] = u[f];
       }
       phys_to_eigen<double>(u, a.is64[k], a.ss64[k], e);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int i = q * K1 + k;
-        W64[i] = a.dhalf[k] * e[q];
-        WS[i] = cvt<T>(W64[i]);
+      for (int q = 0; q < 3; ++q) a.wg[q * K1 + k] = a.dhalf[k] * e[q];
+    }
+    if (j == 0) {
+      for (int t = threadIdx.x; t < 3 * (H - K1); t += BLOCK) {
+        const int f = t / (H - K1), k = K1 + t % (H - K1);
+        gout[f * H + k] = {0.0, 0.0};
+        uout[f * H + k] = {0.0, 0.0};
       }
     }
+    if (!grid_barrier(a.count, a.status, epoch)) return;
+    for (int i = threadIdx.x; i < 3 * K1; i += BLOCK) WS[i] = cvt<T>(ldcg_c(a.wg + i));
     __syncthreads();
   }
 }
@@ -196,7 +235,7 @@ __global__ void __launch_bounds__(BLOCK) chain_kernel(ChainArgs a, NbarTabs<T> t
 template <typename T, int LOGN>
 arp_status launch_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
   constexpr int BLOCK = FineBlock<LOGN>::value;
-  const size_t smem = chain_smem_bytes<T>(1 << LOGN);
+  const size_t smem = chain_smem_bytes<T>(LOGN);
   auto kern = chain_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "chain: shared-memory attribute");
@@ -205,10 +244,11 @@ arp_status launch_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) return check_cuda(c, e, "chain: occupancy");
   if ((long long)per_sm * sms < c->P) return fail(c, ARP_EINVAL, "chain: grid cannot be co-resident");
+  if ((c->K1 + c->P - 1) / c->P > 64) return fail(c, ARP_EINVAL, "chain: too many wavenumbers per block");
   e = cudaMemsetAsync(c->sync, 0, 4 * sizeof(unsigned), s);
   if (e != cudaSuccess) return check_cuda(c, e, "chain: reset");
-  ChainArgs a{V, U, Gc, c->partial, c->part2, c->sync, c->sync + 1, c->slices, c->M, c->qc, c->skip_arrival, c->dT,
-              c->inv_sig64, c->sk_sig64, c->dhalf, c->gphase};
+  ChainArgs a{V, U, Gc, c->partial, c->part2, c->W, c->W2, c->sync, c->sync + 1, c->slices, c->M, c->qc,
+              c->skip_arrival, c->dT, c->inv_sig64, c->sk_sig64, c->dhalf, c->gphase};
   c->skip_arrival = 0;
   NbarTabs<T> tb = nbar_tabs<T>(c);
   void* args[] = {&a, &tb};

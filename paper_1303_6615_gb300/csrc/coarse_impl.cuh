@@ -24,9 +24,9 @@ struct NbarTabs {
 };
 
 template <typename T>
-inline size_t nbar_smem_bytes(int N) {
-  const int K1 = (N - 1) / 3 + 1;
-  return (size_t)(2 * N + N / 2 + 6 * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
+inline size_t nbar_smem_bytes(int logn) {
+  const int K1 = ((1 << logn) - 1) / 3 + 1;
+  return (size_t)(lanes_and_twiddles<T>(logn) + 6 * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
 }
 
 // Evaluates, for the eigen state WS (shared memory, visible to the block),
@@ -89,9 +89,9 @@ __global__ void __launch_bounds__(BLOCK) nbar_partial_kernel(const cd* __restric
   constexpr int K1 = K + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* Z0 = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* Z1 = Z0 + N;
-  cpx<T>* TW = Z1 + N;
-  cpx<T>* WS = TW + N / 2;
+  cpx<T>* Z1 = Z0 + padded_len<T>(N);
+  cpx<T>* TW = Z1 + padded_len<T>(N);
+  cpx<T>* WS = TW + twiddle_count(LOGN);
   cpx<T>* ACC = WS + 3 * K1;
   T* IS = reinterpret_cast<T*>(ACC + 3 * K1);
   T* SS = IS + K1;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(BLOCK) nbar_partial_kernel(const cd* __restric
   const int m0 = min(M, p * chunk);
   const int m1 = min(M, m0 + chunk);
   const cd* w = W + (size_t)b * 3 * K1;
-  for (int t = threadIdx.x; t < N / 2; t += BLOCK) TW[t] = tb.tw[t];
+  for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TW[t] = tb.tw[t];
   for (int k = threadIdx.x; k < K1; k += BLOCK) {
     IS[k] = tb.is[k];
     SS[k] = tb.ss[k];
@@ -127,7 +127,7 @@ inline NbarTabs<float> nbar_tabs<float>(const arp_ctx* c) {
 template <typename T, int LOGN>
 arp_status launch_nbar_n(arp_ctx* c, const cd* W, cd* partial, int batch, cudaStream_t s) {
   constexpr int BLOCK = FineBlock<LOGN>::value;
-  const size_t smem = nbar_smem_bytes<T>(1 << LOGN);
+  const size_t smem = nbar_smem_bytes<T>(LOGN);
   auto kern = nbar_partial_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "nbar: shared-memory attribute");

@@ -30,7 +30,7 @@ struct arp_ctx {
   arp::cd* etd64 = nullptr;      // [6][3][K1]: E, E2, Q, f1, f2x2, f3
   arp::cf* etd32 = nullptr;
   arp::cf* E_lo32 = nullptr;     // [3][K1]: E - (double)(float)E, rounded to float
-  arp::cd* tw64 = nullptr;       // [N/2] e^{-2 pi i t/N}
+  arp::cd* tw64 = nullptr;       // [N] (twiddle_count(logN) used): per-stage FFT twiddles
   arp::cf* tw32 = nullptr;
   arp::cd* phase64 = nullptr;    // [M][3][K1] e^{-i omega s_m}
   arp::cf* phase32 = nullptr;

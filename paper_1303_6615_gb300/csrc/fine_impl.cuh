@@ -50,7 +50,7 @@ struct FineTabs {
 
 template <int LOGN> struct FineBlock {
   static constexpr int N = 1 << LOGN;
-  static constexpr int value = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
+  static constexpr int value = N / 4 < 32 ? 32 : (N / 4 > 512 ? 512 : N / 4);
 };
 
 template <typename T>
@@ -58,11 +58,22 @@ constexpr int fine_mode_arrays() {
   return std::is_same<T, float>::value ? 6 : 4;  // u, N(u), a1, acc (+ u_lo, acc_lo)
 }
 
+// Shared memory of one state's transform: two padded lanes and the twiddle tables.
 template <typename T>
-inline size_t fine_smem_bytes(int N) {
-  const int K1 = (N - 1) / 3 + 1;
-  return (size_t)(2 * N + N / 2 + 3 * fine_mode_arrays<T>() * K1) * sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
+constexpr int lanes_and_twiddles(int logn) {
+  return 2 * padded_len<T>(1 << logn) + twiddle_count(logn);
 }
+
+// Shared-memory layout of the fine sweep; the twiddle tables move to global
+// memory (read through L1) when they would not fit (FP64 at N = 2048).
+template <typename T, int LOGN>
+struct FineLayout {
+  static constexpr int K1 = ((1 << LOGN) - 1) / 3 + 1;
+  static constexpr size_t kWithTw = (size_t)(lanes_and_twiddles<T>(LOGN) + 3 * fine_mode_arrays<T>() * K1) *
+                                        sizeof(cpx<T>) + (size_t)2 * K1 * sizeof(T);
+  static constexpr bool kTwShared = kWithTw <= 227 * 1024;
+  static constexpr size_t kBytes = kTwShared ? kWithTw : kWithTw - (size_t)twiddle_count(LOGN) * sizeof(cpx<T>);
+};
 
 // Reads state b of a physical FP64 buffer [batch][3][H] and returns its eigen
 // amplitudes at wavenumber k (k = 0 coefficients taken as real).
@@ -95,10 +106,12 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
   constexpr int K = (N - 1) / 3;
   constexpr int K1 = K + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kTwShared = FineLayout<T, LOGN>::kTwShared;
   cpx<T>* Z0 = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* Z1 = Z0 + N;
-  cpx<T>* TW = Z1 + N;
-  cpx<T>* U = TW + N / 2;
+  cpx<T>* Z1 = Z0 + padded_len<T>(N);
+  cpx<T>* TWs = Z1 + padded_len<T>(N);
+  const cpx<T>* TW = kTwShared ? TWs : tb.tw;
+  cpx<T>* U = TWs + (kTwShared ? twiddle_count(LOGN) : 0);
   cpx<T>* NU = U + 3 * K1;
   cpx<T>* A1 = NU + 3 * K1;
   cpx<T>* ACC = A1 + 3 * K1;
@@ -109,7 +122,8 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
   T* SS = IS + K1;
 
   const cd* src = in + (size_t)blockIdx.x * 3 * H;
-  for (int t = threadIdx.x; t < N / 2; t += BLOCK) TW[t] = tb.tw[t];
+  if (kTwShared)
+    for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TWs[t] = tb.tw[t];
   for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
     if (k <= K) {
       const T is = tb.is[k], ss = tb.ss[k];
@@ -240,7 +254,7 @@ inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
 template <typename T, int LOGN>
 arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
   constexpr int BLOCK = FineBlock<LOGN>::value;
-  const size_t smem = fine_smem_bytes<T>(1 << LOGN);
+  const size_t smem = FineLayout<T, LOGN>::kBytes;
   auto kern = fine_sweep_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");

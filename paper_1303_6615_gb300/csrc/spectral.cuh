@@ -7,7 +7,7 @@
 //           Z0 = v1 + i h and Z1 = v1_x + i v2_x (each lane carries two real
 //           fields of like magnitude, so neither inherits the other's rounding
 //           error; negative k by Hermitian symmetry); zero above K.
-//   inverse length-N complex DFT (sign +) of Z0 and Z1 as in-place radix-4/2
+//   inverse length-N complex DFT (sign +) of Z0 and Z1 as in-place radix-8
 //           decimation-in-frequency stages: natural-order spectrum in,
 //           physical samples out in digit-reversed order.
 //   product pointwise (order does not matter): Z0 <- (-v1 v1_x) + i(-v1 v2_x),
@@ -16,6 +16,12 @@
 //   forward length-N complex DFT (sign -) as in-place decimation-in-time
 //           stages in the mirrored order: digit-reversed samples in, natural
 //           spectrum out.
+// The stage spans are N, N/8, ... down to a middle span of 8, 4 or 2 (the
+// remainder of log2 N by 3); each outer stage is one shared-memory round trip
+// of radix-8 butterflies held in registers.  Lane arrays are stored padded
+// (one slot every 16 float or 8 double elements) so that every stage's
+// accesses are free of bank conflicts, and each outer stage reads its twiddles
+// W_L^{qj}, q = 1..7, from its own table laid out q-major (consecutive j).
 //   unpack  per k <= K: P1 = (Z0_k + conj Z0_{-k})/2, P2 = (Z0_k - conj Z0_{-k})/(2i),
 //           P3 = Z1_k; N_k = (P1, P2, i k P3)/N; b_k = R_k^H N_k.
 //
@@ -54,6 +60,31 @@ __device__ __forceinline__ void phys_to_eigen(const cpx<T> u[3], T is, T ss, cpx
   a[0] = r2 * (u[0] - iv2 - hs);
 }
 
+// Padded position of element i of a lane array: one slot every 2^kShift elements.
+template <typename T> struct Pad;
+template <> struct Pad<float> { static constexpr int kShift = 4; };
+template <> struct Pad<double> { static constexpr int kShift = 3; };
+template <typename T>
+__host__ __device__ __forceinline__ constexpr int pidx(int i) {
+  return i + (i >> Pad<T>::kShift);
+}
+template <typename T>
+__host__ __device__ constexpr int padded_len(int n) {
+  return n + (n >> Pad<T>::kShift);
+}
+
+// Stage plan for N = 2^LOGN: middle span 2^kLogMid (8 if 3 | log2 N, else 2
+// or 4), outer radix-8 stages at spans 2^logL, logL = LOGN, LOGN-3, ... > kLogMid.
+__host__ __device__ constexpr int stage_log_mid(int logn) { return (logn % 3 == 0) ? 3 : logn % 3; }
+// Offset of the twiddle table of the outer stage of span 2^logL (tables of the
+// larger spans first; each holds 7 L/8 entries).
+__host__ __device__ constexpr int twiddle_offset(int logn, int logL) {
+  int off = 0;
+  for (int l = logn; l > logL; l -= 3) off += 7 * ((1 << l) / 8);
+  return off;
+}
+__host__ __device__ constexpr int twiddle_count(int logn) { return twiddle_offset(logn, stage_log_mid(logn)); }
+
 // Writes the inverse-transform input of wavenumber k (0 <= k <= K) for the
 // eigen amplitudes a: Z0 = v1 + i h, Z1 = v1_x + i v2_x at bins k and N-k.
 template <typename T, int N>
@@ -70,10 +101,10 @@ __device__ __forceinline__ void pack_mode(cpx<T>* Z0, cpx<T>* Z1, int k, const c
     Z0[0] = mk<T>(A.x, D.x);
     Z1[0] = mk<T>((T)0, (T)0);
   } else {
-    Z0[k] = A + mul_i(D);
-    Z0[N - k] = conj(A) + mul_i(conj(D));
-    Z1[k] = B + mul_i(C);
-    Z1[N - k] = conj(B) + mul_i(conj(C));
+    Z0[pidx<T>(k)] = A + mul_i(D);
+    Z0[pidx<T>(N - k)] = conj(A) + mul_i(conj(D));
+    Z1[pidx<T>(k)] = B + mul_i(C);
+    Z1[pidx<T>(N - k)] = conj(B) + mul_i(conj(C));
   }
 }
 
@@ -81,10 +112,10 @@ __device__ __forceinline__ void pack_mode(cpx<T>* Z0, cpx<T>* Z1, int k, const c
 template <typename T, int N>
 __device__ __forceinline__ void zero_mode(cpx<T>* Z0, cpx<T>* Z1, int k) {
   const cpx<T> z = mk<T>(0, 0);
-  Z0[k] = z;
-  Z1[k] = z;
-  Z0[N - k] = z;
-  Z1[N - k] = z;
+  Z0[pidx<T>(k)] = z;
+  Z1[pidx<T>(k)] = z;
+  Z0[pidx<T>(N - k)] = z;
+  Z1[pidx<T>(N - k)] = z;
 }
 
 // Reads the forward-transform output at wavenumber k (0 <= k <= K) and returns
@@ -99,22 +130,15 @@ __device__ __forceinline__ void unpack_mode(const cpx<T>* Z0, const cpx<T>* Z1, 
     n3[1] = mk<T>(q.y * inv_n, 0);
     n3[2] = mk<T>(0, 0);
   } else {
-    cpx<T> q = Z0[k];
-    cpx<T> qm = conj(Z0[N - k]);
-    cpx<T> r = Z1[k];
+    cpx<T> q = Z0[pidx<T>(k)];
+    cpx<T> qm = conj(Z0[pidx<T>(N - k)]);
+    cpx<T> r = Z1[pidx<T>(k)];
     const T half_n = (T)0.5 * inv_n;
     n3[0] = half_n * (q + qm);
     n3[1] = half_n * mul_mi(q - qm);
     n3[2] = ((T)k * inv_n) * mul_i(r);
   }
   phys_to_eigen(n3, is, ss, b);
-}
-
-// Twiddle W_N^t = e^{sign 2 pi i t / N} from the table tw[t] = e^{-2 pi i t/N}, t < N/2.
-template <typename T, int N, int SIGN>
-__device__ __forceinline__ cpx<T> twiddle(const cpx<T>* tw, int t) {
-  cpx<T> w = (t < N / 2) ? tw[t] : mk<T>(-tw[t - N / 2].x, -tw[t - N / 2].y);
-  return SIGN > 0 ? conj(w) : w;
 }
 
 // Length-4 DFT with root e^{sign 2 pi i/4} = sign * i.
@@ -128,39 +152,56 @@ __device__ __forceinline__ void dft4(cpx<T>& x0, cpx<T>& x1, cpx<T>& x2, cpx<T>&
   x3 = a1 - a3;
 }
 
-// One radix-4 stage on both lanes, span L (L/4 butterflies per group).
-// DIF: DFT then twiddle W_L^{qj}; DIT: twiddle then DFT.
+// Length-8 DFT with root w = e^{sign 2 pi i/8}: two length-4 DFTs of the even
+// and odd entries, combined with w^1 = (1 + sign i)/sqrt2, w^2 = sign i,
+// w^3 = (-1 + sign i)/sqrt2.
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft8(cpx<T> x[8]) {
+  cpx<T> e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  cpx<T> o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<T, SIGN>(e0, e1, e2, e3);
+  dft4<T, SIGN>(o0, o1, o2, o3);
+  const T r = Consts<T>::rsqrt2();
+  const cpx<T> t1 = SIGN > 0 ? r * (o1 + mul_i(o1)) : r * (o1 - mul_i(o1));
+  const cpx<T> t2 = SIGN > 0 ? mul_i(o2) : mul_mi(o2);
+  const cpx<T> t3 = SIGN > 0 ? r * (mul_i(o3) - o3) : r * (mk<T>(-o3.x, -o3.y) - mul_i(o3));
+  x[0] = e0 + o0;
+  x[4] = e0 - o0;
+  x[1] = e1 + t1;
+  x[5] = e1 - t1;
+  x[2] = e2 + t2;
+  x[6] = e2 - t2;
+  x[3] = e3 + t3;
+  x[7] = e3 - t3;
+}
+
+// One outer radix-8 stage on both lanes, span L = 2^logL (L/8 butterflies per
+// group).  tw: this stage's table, tw[(q-1) L/8 + j] = e^{-2 pi i q j / L}.
+// DIF (inverse, sign +): DFT then multiply by conj(tw); DIT (forward, sign -):
+// multiply by tw then DFT.
 template <typename T, int N, int BLOCK, int SIGN, bool DIF>
-__device__ __forceinline__ void radix4_stage(cpx<T>* Z0, cpx<T>* Z1, const cpx<T>* tw, int logL) {
-  const int quarter = 1 << (logL - 2);
-  const int tstride = N >> logL;  // N / L
-  constexpr int NB = N / 4;
+__device__ __forceinline__ void radix8_stage(cpx<T>* Z0, cpx<T>* Z1, const cpx<T>* tw, int logL) {
+  const int e = 1 << (logL - 3);
+  constexpr int NB = N / 8;
   for (int item = threadIdx.x; item < 2 * NB; item += BLOCK) {
     cpx<T>* Z = (item < NB) ? Z0 : Z1;
     const int bidx = (item < NB) ? item : item - NB;
-    const int j = bidx & (quarter - 1);
-    const int base = ((bidx >> (logL - 2)) << logL) + j;
-    cpx<T> x0 = Z[base], x1 = Z[base + quarter], x2 = Z[base + 2 * quarter], x3 = Z[base + 3 * quarter];
-    const int t = j * tstride;
-    if (DIF) {
-      dft4<T, SIGN>(x0, x1, x2, x3);
-      if (j) {
-        x1 = x1 * twiddle<T, N, SIGN>(tw, t);
-        x2 = x2 * twiddle<T, N, SIGN>(tw, 2 * t);
-        x3 = x3 * twiddle<T, N, SIGN>(tw, 3 * t);
-      }
-    } else {
-      if (j) {
-        x1 = x1 * twiddle<T, N, SIGN>(tw, t);
-        x2 = x2 * twiddle<T, N, SIGN>(tw, 2 * t);
-        x3 = x3 * twiddle<T, N, SIGN>(tw, 3 * t);
-      }
-      dft4<T, SIGN>(x0, x1, x2, x3);
+    const int j = bidx & (e - 1);
+    const int base = ((bidx >> (logL - 3)) << logL) + j;
+    cpx<T> x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = Z[pidx<T>(base + q * e)];
+    if (!DIF && j) {
+#pragma unroll
+      for (int q = 1; q < 8; ++q) x[q] = x[q] * tw[(q - 1) * e + j];
     }
-    Z[base] = x0;
-    Z[base + quarter] = x1;
-    Z[base + 2 * quarter] = x2;
-    Z[base + 3 * quarter] = x3;
+    dft8<T, SIGN>(x);
+    if (DIF && j) {
+#pragma unroll
+      for (int q = 1; q < 8; ++q) x[q] = x[q] * conj(tw[(q - 1) * e + j]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Z[pidx<T>(base + q * e)] = x[q];
   }
 }
 
@@ -172,63 +213,66 @@ __device__ __forceinline__ void products(cpx<T>& z0, cpx<T>& z1) {
   z1 = mk<T>(-h * v1, (T)0);
 }
 
-// The fused middle stage: last inverse (DIF) stage, whose twiddles are all 1,
-// the products, and the first forward (DIT) stage, which touches the same
-// positions.  Span 2 when log2 N is odd, else 4.
+// The fused middle stage (span 2^LOGMID, twiddles all 1): last inverse DFT,
+// products, first forward DFT, on the same positions.
 template <typename T, int LOGN, int BLOCK>
 __device__ __forceinline__ void middle_stage(cpx<T>* Z0, cpx<T>* Z1) {
   constexpr int N = 1 << LOGN;
-  if (LOGN & 1) {
-    for (int i = threadIdx.x; i < N / 2; i += BLOCK) {
-      cpx<T> a0 = Z0[2 * i], a1 = Z0[2 * i + 1];
-      cpx<T> b0 = Z1[2 * i], b1 = Z1[2 * i + 1];
-      cpx<T> s = a0 + a1, d = a0 - a1;
-      cpx<T> t = b0 + b1, e = b0 - b1;
-      products(s, t);
-      products(d, e);
-      Z0[2 * i] = s + d;
-      Z0[2 * i + 1] = s - d;
-      Z1[2 * i] = t + e;
-      Z1[2 * i + 1] = t - e;
+  constexpr int LOGMID = stage_log_mid(LOGN);
+  constexpr int R = 1 << LOGMID;
+  for (int i = threadIdx.x; i < N / R; i += BLOCK) {
+    cpx<T> a[8], b[8];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      a[q] = Z0[pidx<T>(R * i + q)];
+      b[q] = Z1[pidx<T>(R * i + q)];
     }
-  } else {
-    for (int i = threadIdx.x; i < N / 4; i += BLOCK) {
-      cpx<T> a0 = Z0[4 * i], a1 = Z0[4 * i + 1], a2 = Z0[4 * i + 2], a3 = Z0[4 * i + 3];
-      cpx<T> b0 = Z1[4 * i], b1 = Z1[4 * i + 1], b2 = Z1[4 * i + 2], b3 = Z1[4 * i + 3];
-      dft4<T, +1>(a0, a1, a2, a3);
-      dft4<T, +1>(b0, b1, b2, b3);
-      products(a0, b0);
-      products(a1, b1);
-      products(a2, b2);
-      products(a3, b3);
-      dft4<T, -1>(a0, a1, a2, a3);
-      dft4<T, -1>(b0, b1, b2, b3);
-      Z0[4 * i] = a0; Z0[4 * i + 1] = a1; Z0[4 * i + 2] = a2; Z0[4 * i + 3] = a3;
-      Z1[4 * i] = b0; Z1[4 * i + 1] = b1; Z1[4 * i + 2] = b2; Z1[4 * i + 3] = b3;
+    if (R == 8) {
+      dft8<T, +1>(a);
+      dft8<T, +1>(b);
+    } else if (R == 4) {
+      dft4<T, +1>(a[0], a[1], a[2], a[3]);
+      dft4<T, +1>(b[0], b[1], b[2], b[3]);
+    } else {
+      const cpx<T> s = a[0] + a[1], d = a[0] - a[1], t = b[0] + b[1], u = b[0] - b[1];
+      a[0] = s; a[1] = d; b[0] = t; b[1] = u;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) products(a[q], b[q]);
+    if (R == 8) {
+      dft8<T, -1>(a);
+      dft8<T, -1>(b);
+    } else if (R == 4) {
+      dft4<T, -1>(a[0], a[1], a[2], a[3]);
+      dft4<T, -1>(b[0], b[1], b[2], b[3]);
+    } else {
+      const cpx<T> s = a[0] + a[1], d = a[0] - a[1], t = b[0] + b[1], u = b[0] - b[1];
+      a[0] = s; a[1] = d; b[0] = t; b[1] = u;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      Z0[pidx<T>(R * i + q)] = a[q];
+      Z1[pidx<T>(R * i + q)] = b[q];
     }
   }
 }
 
-// Span exponents of the outer stages: inverse stages run logL = LOGN, LOGN-2,
-// ... > kLogMid; forward stages run logL = kLogMid+2, ..., LOGN.
-template <int LOGN> struct StagePlan { static constexpr int kLogMid = (LOGN & 1) ? 1 : 2; };
-
 // Inverse transform, products and forward transform of the lanes Z0, Z1
-// (entry and exit synchronised).  tw: e^{-2 pi i t/N}, t < N/2.
+// (entry and exit synchronised).  TW: the outer stages' twiddle tables.
 template <typename T, int LOGN, int BLOCK>
-__device__ __forceinline__ void nonlinear_transform(cpx<T>* Z0, cpx<T>* Z1, const cpx<T>* tw) {
+__device__ __forceinline__ void nonlinear_transform(cpx<T>* Z0, cpx<T>* Z1, const cpx<T>* TW) {
   constexpr int N = 1 << LOGN;
-  constexpr int LOGMID = StagePlan<LOGN>::kLogMid;
-#pragma unroll 1
-  for (int logL = LOGN; logL > LOGMID; logL -= 2) {
-    radix4_stage<T, N, BLOCK, +1, true>(Z0, Z1, tw, logL);
+  constexpr int LOGMID = stage_log_mid(LOGN);
+#pragma unroll
+  for (int logL = LOGN; logL > LOGMID; logL -= 3) {
+    radix8_stage<T, N, BLOCK, +1, true>(Z0, Z1, TW + twiddle_offset(LOGN, logL), logL);
     __syncthreads();
   }
   middle_stage<T, LOGN, BLOCK>(Z0, Z1);
   __syncthreads();
-#pragma unroll 1
-  for (int logL = LOGMID + 2; logL <= LOGN; logL += 2) {
-    radix4_stage<T, N, BLOCK, -1, false>(Z0, Z1, tw, logL);
+#pragma unroll
+  for (int logL = LOGMID + 3; logL <= LOGN; logL += 3) {
+    radix8_stage<T, N, BLOCK, -1, false>(Z0, Z1, TW + twiddle_offset(LOGN, logL), logL);
     __syncthreads();
   }
 }

@@ -1,7 +1,7 @@
 // tables.cu -- per-context tables, computed on the device in FP64 and rounded
 // for the FP32 path:
 //   * eigenvector constants of L_k (Sec. 6.1);
-//   * FFT twiddles e^{-2 pi i t/N};
+//   * per-stage FFT twiddles e^{-2 pi i q j / L} of the radix-8 stages;
 //   * ETDRK4 coefficients (Cox & Matthews) per wavenumber and eigen-branch for
 //     the linear symbol lambda = -i omega/eps - nu k^4 (omega = alpha sigma_k);
 //   * time-average nodes' phases e^{-i omega s_m}, s_m = T0 m/M, and weights
@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "context.h"
+#include "spectral.cuh"
 
 namespace arp {
 namespace {
@@ -71,11 +72,20 @@ __global__ void eigen_consts_kernel(int K1, double s, double* is64, double* ss64
   ss32[k] = (float)(sk / sig);
 }
 
-__global__ void twiddle_kernel(int N, cd* tw64, cf* tw32) {
+// Per-stage FFT twiddle tables: for each outer stage of span L = 2^logL,
+// entries [(q-1) L/8 + j] = e^{-2 pi i q j / L}, q = 1..7, j < L/8.
+__global__ void twiddle_kernel(int logn, cd* tw64, cf* tw32) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N / 2) return;
+  if (t >= twiddle_count(logn)) return;
+  int off = 0, logL = logn;
+  while (t >= off + 7 * ((1 << logL) / 8)) {
+    off += 7 * ((1 << logL) / 8);
+    logL -= 3;
+  }
+  const int e = (1 << logL) / 8;
+  const int q = (t - off) / e + 1, j = (t - off) % e;
   double s, c;
-  sincospi(-2.0 * (double)t / (double)N, &s, &c);
+  sincospi(-2.0 * (double)(q * j) / (double)(1 << logL), &s, &c);
   tw64[t] = {c, s};
   tw32[t] = {(float)c, (float)s};
 }
@@ -193,7 +203,7 @@ arp_status build_tables(arp_ctx* c, cudaStream_t st) {
   const int tb = 128;
   eigen_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->inv_sig64, c->sk_sig64, c->inv_sig32,
                                                            c->sk_sig32);
-  twiddle_kernel<<<(c->N / 2 + tb - 1) / tb, tb, 0, st>>>(c->N, c->tw64, c->tw32);
+  twiddle_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw64, c->tw32);
   etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32);
   weights_kernel<<<1, 256, 0, st>>>(c->M, c->weight64, c->weight32);
   phase_kernel<<<dim3((c->K1 + tb - 1) / tb, c->M), tb, 0, st>>>(c->M, c->K1, s, T0, c->phase64, c->phase32);
