@@ -24,6 +24,8 @@
 // block returns, so a lost block can never hang the GPU.
 #pragma once
 
+#include <type_traits>
+
 #include "coarse_impl.cuh"
 
 namespace arp {
@@ -39,21 +41,29 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // Barrier across the co-resident blocks of a cooperative launch.  `epoch` is
 // the block's running target (gridDim.x per barrier); returns false if the
 // status word is set (a timeout here or elsewhere).  The block barrier orders
-// every thread's writes before thread 0's fence and arrival; thread 0's fence
-// after the wait orders the block's later reads.
+// every thread's writes before thread 0's release-add arrival; thread 0's
+// acquire loads of the counter order the block's later reads.
+__device__ __forceinline__ void arrive_release(unsigned* p) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* status, unsigned& epoch, bool arrive = true) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     epoch += gridDim.x;
-    __threadfence();
-    if (arrive) atomicAdd(count, 1u);
+    if (arrive) arrive_release(count);
     const unsigned long long t0 = globaltimer_ns();
     int good = 1;
     for (;;) {
-      const unsigned v = *(volatile unsigned*)count;
+      const unsigned v = load_acquire(count);
       if ((int)(v - epoch) >= 0) break;
-      if (*(volatile unsigned*)status != 0u) {
+      if (load_acquire(status) != 0u) {
         good = 0;
         break;
       }
@@ -63,7 +73,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* status, 
         break;
       }
     }
-    __threadfence();
     ok = good;
   }
   __syncthreads();
@@ -236,7 +245,7 @@ template <typename T, int LOGN>
 arp_status launch_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
   constexpr int BLOCK = FineBlock<LOGN>::value;
   const size_t smem = chain_smem_bytes<T>(LOGN);
-  auto kern = chain_kernel<T, LOGN, BLOCK>;
+  const void* kern = (const void*)chain_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "chain: shared-memory attribute");
   int per_sm = 0, sms = 0;
@@ -252,7 +261,7 @@ arp_status launch_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s
   c->skip_arrival = 0;
   NbarTabs<T> tb = nbar_tabs<T>(c);
   void* args[] = {&a, &tb};
-  e = cudaLaunchCooperativeKernel((const void*)kern, dim3(c->P), dim3(BLOCK), args, smem, s);
+  e = cudaLaunchCooperativeKernel(kern, dim3(c->P), dim3(BLOCK), args, smem, s);
   return check_cuda(c, e, "chain: cooperative launch");
 }
 

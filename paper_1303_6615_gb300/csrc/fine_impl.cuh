@@ -234,6 +234,122 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
   }
 }
 
+// FP32 fine sweep with the ETDRK4 state in registers: thread t owns the
+// wavenumbers k = t + r BLOCK (r < MPT), holding u (float pair), N(u), a1 and
+// the update sum (float pair) for the three branches; shared memory holds only
+// the two FFT lanes, the twiddle tables and the eigenvector constants.
+template <int LOGN, int BLOCK>
+struct F32Layout {
+  static constexpr int K1 = ((1 << LOGN) - 1) / 3 + 1;
+  static constexpr int kMPT = (K1 + BLOCK - 1) / BLOCK;
+  static constexpr size_t kBytes = (size_t)lanes_and_twiddles<float>(LOGN) * sizeof(cf) + (size_t)2 * K1 * sizeof(float);
+};
+
+template <int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
+                                                               int steps, FineTabs<float> tb) {
+  using T = float;
+  constexpr int N = 1 << LOGN;
+  constexpr int H = N / 2 + 1;
+  constexpr int K = (N - 1) / 3;
+  constexpr int K1 = K + 1;
+  constexpr int MPT = F32Layout<LOGN, BLOCK>::kMPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf* Z0 = reinterpret_cast<cf*>(smem_raw);
+  cf* Z1 = Z0 + padded_len<T>(N);
+  cf* TW = Z1 + padded_len<T>(N);
+  T* IS = reinterpret_cast<T*>(TW + twiddle_count(LOGN));
+  T* SS = IS + K1;
+
+  cf u[MPT][3], ulo[MPT][3], nu[MPT][3], a1[MPT][3], acc[MPT][3], acclo[MPT][3];
+  const cd* src = in + (size_t)blockIdx.x * 3 * H;
+  for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TW[t] = tb.tw[t];
+#pragma unroll
+  for (int r = 0; r < MPT; ++r) {
+    const int k = threadIdx.x + r * BLOCK;
+    if (k <= K) {
+      const T is = tb.is[k], ss = tb.ss[k];
+      IS[k] = is;
+      SS[k] = ss;
+      cd a[3];
+      load_eigen64(src, H, k, tb.is64[k], tb.ss64[k], a);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        u[r][q] = cvt<float>(a[q]);
+        ulo[r][q] = cvt<float>(a[q] - cvt<double>(u[r][q]));
+      }
+      pack_mode<T, N>(Z0, Z1, k, u[r], is, ss);
+    }
+  }
+  for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+  __syncthreads();
+
+  const EtdView<T> e = tb.etd;
+#pragma unroll 1
+  for (int step = 0; step < steps; ++step) {
+    const bool last = (step == steps - 1);
+#pragma unroll 1
+    for (int stage = 0; stage < 4; ++stage) {
+      nonlinear_transform<T, LOGN, BLOCK>(Z0, Z1, TW);
+      const bool pack_next = !(last && stage == 3);
+#pragma unroll
+      for (int r = 0; r < MPT; ++r) {
+        const int k = threadIdx.x + r * BLOCK;
+        if (k > K) continue;
+        const T is = IS[k], ss = SS[k];
+        cf bn[3], nx[3];
+        unpack_mode<T, N>(Z0, Z1, k, is, ss, bn);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int i = q * K1 + k;
+          if (stage == 0) {
+            nu[r][q] = bn[q];
+            a1[r][q] = ldgc(e.E2 + i) * u[r][q] + ldgc(e.Q + i) * bn[q];
+            const cdf s = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(tb.E_lo + i), u[r][q], ulo[r][q]), ldgc(e.f1 + i) * bn[q]);
+            acc[r][q] = mk<float>(s.re.hi, s.im.hi);
+            acclo[r][q] = mk<float>(s.re.lo, s.im.lo);
+            nx[q] = a1[r][q];
+          } else if (stage == 3) {
+            const cf t = ldgc(e.f3 + i) * bn[q];
+            const df re = df_add_f(df{acc[r][q].x, acclo[r][q].x}, t.x);
+            const df im = df_add_f(df{acc[r][q].y, acclo[r][q].y}, t.y);
+            u[r][q] = mk<float>(re.hi, im.hi);
+            ulo[r][q] = mk<float>(re.lo, im.lo);
+            nx[q] = u[r][q];
+          } else {
+            const cf t = ldgc(e.f2x2 + i) * bn[q];
+            const df re = df_add_f(df{acc[r][q].x, acclo[r][q].x}, t.x);
+            const df im = df_add_f(df{acc[r][q].y, acclo[r][q].y}, t.y);
+            acc[r][q] = mk<float>(re.hi, im.hi);
+            acclo[r][q] = mk<float>(re.lo, im.lo);
+            nx[q] = (stage == 1) ? ldgc(e.E2 + i) * u[r][q] + ldgc(e.Q + i) * bn[q]
+                                 : ldgc(e.E2 + i) * a1[r][q] + ldgc(e.Q + i) * ((T)2 * bn[q] - nu[r][q]);
+          }
+        }
+        if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
+      }
+      if (pack_next)
+        for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+      __syncthreads();
+    }
+  }
+
+  cd* dst = out + (size_t)blockIdx.x * 3 * H;
+#pragma unroll
+  for (int r = 0; r < MPT; ++r) {
+    const int k = threadIdx.x + r * BLOCK;
+    if (k > K) continue;
+    cd a[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) a[q] = cvt<double>(u[r][q]) + cvt<double>(ulo[r][q]);
+    store_phys64(dst, H, k, tb.is64[k], tb.ss64[k], a);
+  }
+  for (int k = K1 + threadIdx.x; k < H; k += BLOCK) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) dst[f * H + k] = {0.0, 0.0};
+  }
+}
+
 template <typename T>
 FineTabs<T> fine_tabs(const arp_ctx* c);
 
@@ -254,12 +370,16 @@ inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
 template <typename T, int LOGN>
 arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
   constexpr int BLOCK = FineBlock<LOGN>::value;
-  const size_t smem = FineLayout<T, LOGN>::kBytes;
-  auto kern = fine_sweep_kernel<T, LOGN, BLOCK>;
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK>::kBytes : FineLayout<T, LOGN>::kBytes;
+  const void* kern = kF32 ? (const void*)fine_sweep_kernel_f32<LOGN, BLOCK> : (const void*)fine_sweep_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");
-  kern<<<batch, BLOCK, smem, s>>>(in, out, c->steps, fine_tabs<T>(c));
-  return check_cuda(c, cudaGetLastError(), "fine: launch");
+  FineTabs<T> tb = fine_tabs<T>(c);
+  int steps = c->steps;
+  void* args[] = {(void*)&in, (void*)&out, &steps, &tb};
+  e = cudaLaunchKernel(kern, dim3(batch), dim3(BLOCK), args, smem, s);
+  return check_cuda(c, e, "fine: launch");
 }
 
 template <typename T>
