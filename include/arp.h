@@ -171,6 +171,29 @@ arp_status arp_destroy(arp_ctx* ctx);
  * arp_create when ctx is NULL); never NULL; valid until the next call. */
 const char* arp_last_error(const arp_ctx* ctx);
 
+/*
+ * arp_coarse_avg_static: the time average of arp_coarse_avg (FP64, F = 1,
+ * T0 = dT/eps) for callers that cannot allocate device memory -- a framework
+ * that owns a fixed device-memory budget and forbids allocation after start-up,
+ * or a latency-critical loop where cudaMalloc's implicit synchronisation is not
+ * acceptable.  It needs no context (arp_create allocates) and allocates
+ * nothing: its tables and workspaces live in one 16 MiB file-scope device array
+ * that every GPU loading the library holds until the process exits.  The paper
+ * has no counterpart to this entry point.
+ *   N, eps, dT, M   as for arp_create (the window is T0 = dT/eps)
+ *   U_in, Nbar_out  device, [batch][3][H] complex doubles, caller-owned
+ * The batch is processed in passes of as many states as the array holds.
+ * Returns ARP_EINVAL for invalid sizes and when the tables plus one state's
+ * workspace exceed the 16 MiB array (e.g. N = 2048 with M = 128); no message
+ * is recorded.  Every call shares the array and overwrites what it needs
+ * before reading it (nothing has to start at zero); calls that overlap on the
+ * GPU (on different streams, or from different threads) race on it.  The
+ * first call on a device looks the array's device address up (once per
+ * device), so that call should come before any stream capture.
+ */
+arp_status arp_coarse_avg_static(int N, double eps, double dT, int M, const double* U_in, double* Nbar_out,
+                                 int batch, void* stream);
+
 /* arp_info: sizes of a context: out[0]=N, out[1]=H, out[2]=K, out[3]=slices,
  * out[4]=M, out[5]=fine steps per slice, out[6]=current level k (-1 before the
  * predictor), out[7]=precision. */

@@ -42,6 +42,8 @@ _SIGS = {
     "arp_destroy": (ctypes.c_int, [_P]),
     "arp_last_error": (ctypes.c_char_p, [_P]),
     "arp_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "arp_coarse_avg_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P,
+                                             _P, ctypes.c_int, _P]),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -137,6 +139,20 @@ def arp_coarse_avg(ctx: int, U_in, Nbar_out, stream=None) -> None:
 
 def arp_coarse_step(ctx: int, U_in, U_out, stream=None) -> None:
     _batch_call("arp_coarse_step", ctx, U_in, U_out, stream)
+
+
+def arp_coarse_avg_static(N: int, eps: float, dT: float, M: int, U_in, Nbar_out, stream=None) -> None:
+    """Time average without a context or any device allocation (see include/arp.h)."""
+    H = N // 2 + 1
+    b = _states(U_in, "U_in", H)
+    if _states(Nbar_out, "Nbar_out", H) != b:
+        raise ValueError("U_in and Nbar_out batch sizes differ")
+    if b and (not U_in.is_cuda or not Nbar_out.is_cuda):
+        raise ValueError("U_in and Nbar_out must be device tensors")
+    st = load_library().arp_coarse_avg_static(N, eps, dT, M, U_in.data_ptr() or None,
+                                              Nbar_out.data_ptr() or None, int(b), _stream(stream))
+    if st != ARP_OK:
+        raise ArpError(st, "arp_coarse_avg_static failed")
 
 
 def arp_set_initial(ctx: int, u0, stream=None) -> None:
