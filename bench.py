@@ -38,7 +38,11 @@ METRIC = "fine grid-pt-steps/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64 peak: the part's nominal 1.25 TFLOP/s (FP64 units are a small fraction of FP32 ones).
 FP64_ALU_PEAK_TFLOPS = 1.25
-CPU_SAMPLE_SLICES = 8
+CPU_SAMPLE_SLICES = 64          # cpu_baseline sample (about 10 s of oracle work)
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fine-sweep kernel on this workload
+# (ncu capture of the current kernel); None where no capture of the current kernel exists.
+FINE_TRAFFIC_BYTES = {"fp32": 2274560, "fp64": None}
+REFERENCE_SAMPLE_SLICES = 8     # per-step sample of the reference arm
 
 
 def flops_per_grid_pt_step(n_grid: int) -> float:
@@ -237,8 +241,9 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "fine_sweep_kernel", "launch_ms": fine_ms,
+                     "frac": achieved / peak, "traffic": FINE_TRAFFIC_BYTES[args.precision],
+                     "kernel": "fine_sweep_kernel_f32" if prec == b.ARP_FP32 else "fine_sweep_kernel",
+                     "launch_ms": fine_ms, "flop_per_launch": flops,
                      "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec == b.ARP_FP32
                                      else "FP64 nominal 1.25 TFLOP/s")},
         "fine_only": {"value": units / (fine_ms / 1e3), "unit": "grid-pt-steps/s", "ms": fine_ms},
@@ -289,12 +294,12 @@ def run_reference(args, rank: int) -> dict | None:
     w = WORKLOAD
     times, units = [], 0
     for i in range(args.warmup + args.steps):
-        dt, units = oracle_iteration_sample(CPU_SAMPLE_SLICES)
+        dt, units = oracle_iteration_sample(REFERENCE_SAMPLE_SLICES)
         if i >= args.warmup:
             times.append(dt)
     total = sum(times)
     value = units * args.steps / total
-    sample = (f"one parareal iteration (fine sweep + G + serial chain) on {CPU_SAMPLE_SLICES} of "
+    sample = (f"one parareal iteration (fine sweep + G + serial chain) on {REFERENCE_SAMPLE_SLICES} of "
               f"{w.slices} slices per step")
     return {
         "impl": "reference",

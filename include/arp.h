@@ -184,7 +184,7 @@ const char* arp_last_error(const arp_ctx* ctx);
  *   U_in, Nbar_out  device, [batch][3][H] complex doubles, caller-owned
  * The batch is processed in passes of as many states as the array holds.
  * Returns ARP_EINVAL for invalid sizes and when the tables plus one state's
- * workspace exceed the 16 MiB array (e.g. N = 2048 with M = 128); no message
+ * workspace exceed the 16 MiB array (e.g. N = 2048 with M = 256); no message
  * is recorded.  Every call shares the array and overwrites what it needs
  * before reading it (nothing has to start at zero); calls that overlap on the
  * GPU (on different streams, or from different threads) race on it.  The
