@@ -66,6 +66,10 @@ typedef enum {
   ARP_OPT_PRECISION = 3,   /* an arp_precision value (default ARP_FP64) */
   ARP_OPT_KMAX = 4,        /* iteration cap used by arp_parareal_solve (default 5) */
   ARP_OPT_TOL = 5,         /* stopping tolerance of arp_parareal_solve (default 0) */
+  ARP_OPT_CHAIN = 6,       /* serial coarse chain: 0 = automatic (one thread-block cluster,
+                              else a cooperative grid with bounded grid barriers, else one
+                              launch per step), 1 = cooperative grid, 2 = launches; all give
+                              the same result up to rounding (default 0) */
   ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook: a non-zero value makes
                                       block 0 of the next coarse-chain launch skip its first
                                       grid-barrier arrival, so every block's bounded wait

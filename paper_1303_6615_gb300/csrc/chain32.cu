@@ -1,10 +1,15 @@
-// chain32.cu -- FP32 instantiation of the persistent coarse-chain kernel.
+// chain32.cu -- FP32 instantiations of the coarse-chain kernels.
 #include "chain_impl.cuh"
+#include "cluster_chain.cuh"
 
 namespace arp {
 
 arp_status launch_chain_f32(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
   return launch_chain_prec<float>(c, U, Gc, V, s);
+}
+
+arp_status launch_cluster_chain_f32(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
+  return launch_cluster_chain_prec<float>(c, U, Gc, V, s);
 }
 
 }  // namespace arp

@@ -1,0 +1,323 @@
+// cluster_chain.cuh -- the serial coarse chain of parareal (Eq. 3.1, the second
+// loop of Algorithm 4) inside one thread-block cluster:
+//     g_n = G(U_n),  U_{n+1} = g_n + V_n,  n = 0..S-1,
+// with G the asymptotic slow solver of Algorithm 2 (two time averages per link).
+//
+// C CTAs (16 where the part allows clusters that large, else 8) form one
+// cluster.  CTA j owns the quadrature nodes [j q, (j+1) q), q = ceil(M/C), and
+// evaluates all of them at once (two FFT lanes per node), then sums their
+// weighted, back-rotated terms in node order.  The sum over CTAs, and the
+// exchange of the next state, are stores into other CTAs' shared memory
+// (distributed shared memory) between hardware cluster barriers -- no
+// global-memory atomics, no spin-waits:
+//   1  every CTA: its nodes' partial sum for the current state WS, stored
+//      into the reduction buffer RED[rank] of each wavenumber's owner CTA
+//   2  cluster barrier
+//   3  CTA j, for its own wavenumbers: the sum of RED over the C ranks (fixed
+//      order), then the FP64 epilogue (midpoint state, or g, U_{n+1}, G cache
+//      and the next w); the result's float copy is stored into WS of every CTA
+//   4  cluster barrier
+// The FP64 state w of a wavenumber lives only in its owner CTA, so every
+// exchanged copy is freshly rounded from FP64.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "coarse_impl.cuh"
+
+namespace arp {
+
+struct ClusterChainArgs {
+  const cd* V;       // [S][3][H] or null (predictor)
+  cd* U;             // [(S+1)][3][H]; U_0 read, U_1..U_S written
+  cd* Gc;            // [S][3][H] written
+  int S, M, q, own;  // links, nodes, nodes per CTA, wavenumbers per CTA
+  int ph_smem;       // node phases staged in shared memory (else read from the table)
+  int tmp_smem;      // per-node terms staged for a balanced node sum (else summed per wavenumber)
+  double dT;
+  const double* is64;
+  const double* ss64;
+  const double* dhalf;
+  const cd* gphase;
+};
+
+template <int LOGN> struct ClusterBlock {
+  static constexpr int value = (1 << LOGN) <= 256 ? 256 : 512;
+};
+
+// Shared memory: FP64 per own wavenumber (w, gphase for 3 branches, V of the
+// link for 3 fields, dhalf, the two eigen constants), the FFT lanes, twiddles,
+// the node phases [q][3][K1] and weights, WS/ACC/EXCH and the eigen constants.
+template <typename T>
+inline size_t cluster_chain_smem_bytes(int logn, int q, int own, int C, bool ph_smem, bool tmp_smem) {
+  const int K1 = ((1 << logn) - 1) / 3 + 1;
+  return (size_t)12 * own * sizeof(cd) + (size_t)3 * own * sizeof(double) +
+         (size_t)(2 * q * padded_len<T>(1 << logn) + twiddle_count(logn) + (ph_smem ? 3 * q * K1 : 0) + 3 * K1 +
+                  (tmp_smem ? 3 * q * K1 : 0) + 3 * C * own) *
+             sizeof(cpx<T>) +
+         (size_t)(2 * K1 + q) * sizeof(T);
+}
+
+template <typename T, int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) chain_cluster_kernel(ClusterChainArgs a, NbarTabs<T> tb) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  constexpr int N = 1 << LOGN;
+  constexpr int H = N / 2 + 1;
+  constexpr int K = (N - 1) / 3;
+  constexpr int K1 = K + 1;
+  constexpr int PL = padded_len<T>(N);
+  const int C = (int)cl.num_blocks();
+  const int j = (int)cl.block_rank();
+  const int q = a.q, own = a.own;
+  const int m0 = min(a.M, j * q);
+  const int nq = min(a.M, m0 + q) - m0;  // nodes of this CTA (may be 0)
+  const int k0 = min(K1, j * own), k1 = min(K1, k0 + own);
+
+  // Layout, each array aligned for its element: complex FP64 arrays first
+  // (16-byte elements), then complex T arrays, then FP64 scalars, then T scalars.
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cd* W64 = reinterpret_cast<cd*>(smem_raw);  // [3][own] FP64 w of the own wavenumbers
+  cd* GPH = W64 + 3 * own;                    // [3][own] e^{-i omega dT/eps}
+  cd* VL = GPH + 3 * own;                     // [3][own] V_n of the link (fields)
+  cd* EP = VL + 3 * own;                      // [3][own] epilogue temporaries
+  cpx<T>* Z = reinterpret_cast<cpx<T>*>(EP + 3 * own);
+  cpx<T>* TW = Z + 2 * q * PL;
+  cpx<T>* PHs = TW + twiddle_count(LOGN);     // [q][3][K1] phases of this CTA's nodes
+  cpx<T>* WS = PHs + (a.ph_smem ? 3 * q * K1 : 0);  // [3][K1] state, written by the owners
+  const cpx<T>* PH = a.ph_smem ? PHs : tb.avg.phase + (size_t)m0 * 3 * K1;
+  cpx<T>* TMP = WS + 3 * K1;                  // [q][3][K1] weighted terms of this CTA's nodes
+  cpx<T>* RED = TMP + (a.tmp_smem ? 3 * q * K1 : 0);  // [C][3][own] partial sums sent by each rank
+  double* DH = reinterpret_cast<double*>(RED + 3 * C * own);  // [own] e^{-nu k^4 dT/2}
+  double* IS64 = DH + own;                    // [own]
+  double* SS64 = IS64 + own;                  // [own]
+  T* IS = reinterpret_cast<T*>(SS64 + own);
+  T* SS = IS + K1;
+  T* WM = SS + K1;                            // [q] weights of this CTA's nodes
+
+  for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TW[t] = tb.tw[t];
+  for (int k = threadIdx.x; k < K1; k += BLOCK) {
+    IS[k] = tb.is[k];
+    SS[k] = tb.ss[k];
+  }
+  if (a.ph_smem)
+    for (int t = threadIdx.x; t < nq * 3 * K1; t += BLOCK) PHs[t] = tb.avg.phase[(size_t)m0 * 3 * K1 + t];
+  for (int d = threadIdx.x; d < nq; d += BLOCK) WM[d] = tb.avg.weight[m0 + d];
+  for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
+    DH[k - k0] = a.dhalf[k];
+    IS64[k - k0] = a.is64[k];
+    SS64[k - k0] = a.ss64[k];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) GPH[b * own + (k - k0)] = a.gphase[b * K1 + k];
+  }
+  // w = e^{dT/2 D} R^H U_0 for the own wavenumbers; its float copy into every CTA's WS
+  for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
+    cd x[3], e[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      x[f] = a.U[f * H + k];
+      if (k == 0) x[f].y = 0.0;
+    }
+    phys_to_eigen<double>(x, a.is64[k], a.ss64[k], e);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) W64[b * own + (k - k0)] = a.dhalf[k] * e[b];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < C * 3 * (k1 - k0); t += BLOCK) {
+    const int c = t / (3 * (k1 - k0)), r3 = t - c * 3 * (k1 - k0);
+    const int b = r3 / (k1 - k0), r = r3 - b * (k1 - k0);
+    cl.map_shared_rank(WS, c)[b * K1 + k0 + r] = cvt<T>(W64[b * own + r]);
+  }
+  cl.sync();
+
+#pragma unroll 1
+  for (int n = 0; n < a.S; ++n) {
+    // V_n of the own wavenumbers, fetched now so its latency hides behind the evaluations
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) VL[f * own + (k - k0)] = a.V ? a.V[((size_t)n * 3 + f) * H + k] : cd{0.0, 0.0};
+    }
+#pragma unroll 1
+    for (int round = 0; round < 2; ++round) {
+      // 1: this CTA's nodes, all at once
+      for (int item = threadIdx.x; item < nq * (N / 2 + 1); item += BLOCK) {
+        const int d = item / (N / 2 + 1), k = item - d * (N / 2 + 1);
+        cpx<T>* Z0 = Z + 2 * d * PL;
+        if (k > K) {
+          zero_mode<T, N>(Z0, Z0 + PL, k);
+          continue;
+        }
+        cpx<T> x[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) x[b] = PH[(d * 3 + b) * K1 + k] * WS[b * K1 + k];
+        pack_mode<T, N>(Z0, Z0 + PL, k, x, IS[k], SS[k]);
+      }
+      __syncthreads();
+      if (nq > 0) nonlinear_transform<T, LOGN, BLOCK>(Z, nq, TW);
+      if (a.tmp_smem) {
+        // weighted, back-rotated term of each (node, wavenumber)
+        for (int item = threadIdx.x; item < nq * K1; item += BLOCK) {
+          const int d = item / K1, k = item - d * K1;
+          cpx<T> bn[3];
+          const cpx<T>* Z0 = Z + 2 * d * PL;
+          unpack_mode<T, N>(Z0, Z0 + PL, k, IS[k], SS[k], bn);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) TMP[(d * 3 + b) * K1 + k] = WM[d] * (conj(PH[(d * 3 + b) * K1 + k]) * bn[b]);
+        }
+        __syncthreads();
+        // node sum in node order, stored into the owner's reduction buffer
+        for (int i = threadIdx.x; i < 3 * K1; i += BLOCK) {
+          cpx<T> s = mk<T>(0, 0);
+          for (int d = 0; d < nq; ++d) s = s + TMP[d * 3 * K1 + i];
+          const int b = i / K1, k = i - b * K1, owner = k / own;
+          cl.map_shared_rank(RED, owner)[(j * 3 + b) * own + (k - owner * own)] = s;
+        }
+      } else {
+        // the same sum, one thread per wavenumber over the nodes in order
+        for (int k = threadIdx.x; k < K1; k += BLOCK) {
+          cpx<T> s[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
+          for (int d = 0; d < nq; ++d) {
+            cpx<T> bn[3];
+            const cpx<T>* Z0 = Z + 2 * d * PL;
+            unpack_mode<T, N>(Z0, Z0 + PL, k, IS[k], SS[k], bn);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) s[b] = s[b] + WM[d] * (conj(PH[(d * 3 + b) * K1 + k]) * bn[b]);
+          }
+          const int owner = k / own;
+#pragma unroll
+          for (int b = 0; b < 3; ++b) cl.map_shared_rank(RED, owner)[(j * 3 + b) * own + (k - owner * own)] = s[b];
+        }
+      }
+      cl.sync();  // 2
+      // 3: own wavenumbers: sum over the ranks in rank order, FP64 epilogue
+      const int no = k1 - k0;
+      for (int t = threadIdx.x; t < 3 * no; t += BLOCK) {
+        const int b = t / no, r = t - b * no;
+        cpx<T> s = mk<T>(0, 0);
+        for (int c = 0; c < C; ++c) s = s + RED[(c * 3 + b) * own + r];
+        const cd sum = cvt<double>(s);
+        if (round == 0)  // midpoint state w + dT/2 k1
+          EP[b * own + r] = W64[b * own + r] + (0.5 * a.dT) * sum;
+        else  // g = e^{-(dT/eps) L} e^{dT/2 D} (w + dT k2), per branch
+          EP[b * own + r] = DH[r] * (GPH[b * own + r] * (W64[b * own + r] + a.dT * sum));
+      }
+      __syncthreads();
+      const bool last = (round == 1 && n == a.S - 1);
+      if (round == 1) {
+        // U_{n+1} = R g + V_n and the G cache, per wavenumber; next w = e^{dT/2 D} R^H U_{n+1}
+        cd* gout = a.Gc + (size_t)n * 3 * H;
+        cd* uout = a.U + (size_t)(n + 1) * 3 * H;
+        for (int r = threadIdx.x; r < no; r += BLOCK) {
+          const int k = k0 + r;
+          cd g[3], u[3], e[3];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) g[b] = EP[b * own + r];
+          eigen_to_phys<double>(g, IS64[r], SS64[r], u);
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            if (k == 0) u[f].y = 0.0;
+            gout[f * H + k] = u[f];
+            u[f] = u[f] + VL[f * own + r];
+            uout[f * H + k] = u[f];
+          }
+          phys_to_eigen<double>(u, IS64[r], SS64[r], e);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            W64[b * own + r] = DH[r] * e[b];
+            EP[b * own + r] = W64[b * own + r];
+          }
+        }
+        if (j == 0) {
+          for (int t = threadIdx.x; t < 3 * (H - K1); t += BLOCK) {
+            const int f = t / (H - K1), k = K1 + t % (H - K1);
+            gout[f * H + k] = {0.0, 0.0};
+            uout[f * H + k] = {0.0, 0.0};
+          }
+        }
+        __syncthreads();
+      }
+      if (last) break;
+      // 4: the float copy of the new own values into every CTA's WS
+      for (int t = threadIdx.x; t < C * 3 * no; t += BLOCK) {
+        const int c = t / (3 * no), r3 = t - c * 3 * no;
+        const int b = r3 / no, r = r3 - b * no;
+        cl.map_shared_rank(WS, c)[b * K1 + k0 + r] = cvt<T>(EP[b * own + r]);
+      }
+      cl.sync();  // 4
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still store into its shared memory
+}
+
+// Launches the cluster chain; ARP_EINVAL (nothing launched) if no cluster of 16
+// or 8 CTAs with this kernel's shared memory can be scheduled.
+template <typename T, int LOGN>
+arp_status launch_cluster_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
+  constexpr int BLOCK = ClusterBlock<LOGN>::value;
+  const void* kern = (const void*)chain_cluster_kernel<T, LOGN, BLOCK>;
+  for (int C : {16, 8}) {
+    const int q = (c->M + C - 1) / C;
+    const int own = (c->K1 + C - 1) / C;
+    // stage what fits: the per-node terms first (balance), then the node phases
+    bool tmp_smem = true, ph_smem = true;
+    size_t smem = cluster_chain_smem_bytes<T>(LOGN, q, own, C, ph_smem, tmp_smem);
+    if (smem > 227 * 1024) {
+      ph_smem = false;
+      smem = cluster_chain_smem_bytes<T>(LOGN, q, own, C, ph_smem, tmp_smem);
+    }
+    if (smem > 227 * 1024) {
+      tmp_smem = false;
+      smem = cluster_chain_smem_bytes<T>(LOGN, q, own, C, ph_smem, tmp_smem);
+    }
+    if (smem > 227 * 1024) continue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    ClusterChainArgs a{V, U, Gc, c->slices, c->M, q, own, ph_smem ? 1 : 0, tmp_smem ? 1 : 0, c->dT, c->inv_sig64,
+                       c->sk_sig64, c->dhalf, c->gphase};
+    NbarTabs<T> tb = nbar_tabs<T>(c);
+    void* args[] = {&a, &tb};
+    e = cudaLaunchKernelExC(&cfg, kern, args);
+    return check_cuda(c, e, "cluster chain: launch");
+  }
+  return fail(c, ARP_EINVAL, "cluster chain: no cluster of 16 or 8 blocks fits");
+}
+
+template <typename T>
+arp_status launch_cluster_chain_prec(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
+  switch (c->logN) {
+    case 3: return launch_cluster_chain_n<T, 3>(c, U, Gc, V, s);
+    case 4: return launch_cluster_chain_n<T, 4>(c, U, Gc, V, s);
+    case 5: return launch_cluster_chain_n<T, 5>(c, U, Gc, V, s);
+    case 6: return launch_cluster_chain_n<T, 6>(c, U, Gc, V, s);
+    case 7: return launch_cluster_chain_n<T, 7>(c, U, Gc, V, s);
+    case 8: return launch_cluster_chain_n<T, 8>(c, U, Gc, V, s);
+    case 9: return launch_cluster_chain_n<T, 9>(c, U, Gc, V, s);
+    case 10: return launch_cluster_chain_n<T, 10>(c, U, Gc, V, s);
+    case 11: return launch_cluster_chain_n<T, 11>(c, U, Gc, V, s);
+    default: return fail(c, ARP_EINVAL, "cluster chain: unsupported grid size");
+  }
+}
+
+}  // namespace arp

@@ -54,7 +54,7 @@ __device__ __forceinline__ void nbar_nodes(const cpx<T>* WS, cpx<T>* ACC, int m0
   __syncthreads();
 #pragma unroll 1
   for (int m = m0; m < m1; ++m) {
-    nonlinear_transform<T, LOGN, BLOCK>(Z0, Z1, TW);
+    nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
     const bool next = (m + 1 < m1);
     const T wm = tb.avg.weight[m];
     for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {

@@ -55,6 +55,7 @@ struct arp_ctx {
   arp::cd* Fb = nullptr;         // F(U_n), n < slices
   arp::cd* V = nullptr;          // F - G
   int skip_arrival = 0;          // one-shot failure-detection test hook
+  int chain_mode = 0;            // ARP_OPT_CHAIN
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;
 
@@ -93,6 +94,9 @@ arp_status coarse_step(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_
 // cooperative persistent launch; Gc_n = G(U_n).  Returns ARP_EINVAL (without
 // launching) if the grid cannot be co-resident.
 arp_status launch_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
+// The same chain inside one thread-block cluster (no grid barriers).  Returns
+// ARP_EINVAL (without launching) if no suitable cluster can be scheduled.
+arp_status launch_cluster_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
 
 // parareal.cu
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);

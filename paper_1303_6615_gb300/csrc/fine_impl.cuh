@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
     const bool last = (step == steps - 1);
 #pragma unroll 1
     for (int stage = 0; stage < 4; ++stage) {
-      nonlinear_transform<T, LOGN, BLOCK>(Z0, Z1, TW);
+      nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
       const bool pack_next = !(last && stage == 3);
       for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
         if (k > K) {
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restr
     const bool last = (step == steps - 1);
 #pragma unroll 1
     for (int stage = 0; stage < 4; ++stage) {
-      nonlinear_transform<T, LOGN, BLOCK>(Z0, Z1, TW);
+      nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
       const bool pack_next = !(last && stage == 3);
 #pragma unroll
       for (int r = 0; r < MPT; ++r) {

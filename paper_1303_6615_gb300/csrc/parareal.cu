@@ -91,11 +91,19 @@ arp_status chain_link(arp_ctx* c, const cd* u, cd* g_out, cd* u_next, const cd* 
   return launch_nbar_reduce(c, kReduceFinal, c->partial, c->W, nullptr, g_out, v, u_next, 1, s);
 }
 
-// The whole serial chain n = 0..S-1: the persistent cooperative kernel, else
-// one link at a time.
+// The whole serial chain n = 0..S-1: one thread-block cluster, else the
+// persistent cooperative kernel, else one link at a time (ARP_OPT_CHAIN
+// restricts the choice; the barrier-timeout test hook needs the cooperative
+// kernel, whose grid barriers are the bounded waits it exercises).
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   const size_t st = (size_t)3 * c->H;
-  arp_status r = launch_chain(c, c->U, c->Gc, V, s);
+  // barrier counter and status word start at zero whichever kernel runs
+  arp_status r = check_cuda(c, cudaMemsetAsync(c->sync, 0, 4 * sizeof(unsigned), s), "chain: status reset");
+  if (r != ARP_OK) return r;
+  r = ARP_EINVAL;
+  if (c->chain_mode == 0 && !c->skip_arrival) r = launch_cluster_chain(c, c->U, c->Gc, V, s);
+  if (r != ARP_EINVAL) return r;
+  if (c->chain_mode <= 1) r = launch_chain(c, c->U, c->Gc, V, s);
   if (r != ARP_EINVAL) return r;
   for (int n = 0; n < c->slices; ++n)
     if ((r = chain_link(c, c->U + n * st, c->Gc + n * st, c->U + (n + 1) * st, V ? V + n * st : nullptr, s)) !=

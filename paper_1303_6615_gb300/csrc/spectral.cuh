@@ -175,22 +175,25 @@ __device__ __forceinline__ void dft8(cpx<T> x[8]) {
   x[7] = e3 - t3;
 }
 
-// One outer radix-8 stage on both lanes, span L = 2^logL (L/8 butterflies per
-// group).  tw: this stage's table, tw[(q-1) L/8 + j] = e^{-2 pi i q j / L}.
+// One outer radix-8 stage on `nlanes` lanes stored back to back (lane l at
+// Z + l * padded_len(N)), span L = 2^logL (L/8 butterflies per group).
+// tw: this stage's table, tw[(q-1) L/8 + j] = e^{-2 pi i q j / L}.
 // DIF (inverse, sign +): DFT then multiply by conj(tw); DIT (forward, sign -):
 // multiply by tw then DFT.
 template <typename T, int N, int BLOCK, int SIGN, bool DIF>
-__device__ __forceinline__ void radix8_stage(cpx<T>* Z0, cpx<T>* Z1, const cpx<T>* tw, int logL) {
-  const int e = 1 << (logL - 3);
+__device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>* tw, int logL) {
+  constexpr int PL = padded_len<T>(N);
   constexpr int NB = N / 8;
-  for (int item = threadIdx.x; item < 2 * NB; item += BLOCK) {
-    cpx<T>* Z = (item < NB) ? Z0 : Z1;
-    const int bidx = (item < NB) ? item : item - NB;
+  const int e = 1 << (logL - 3);
+  for (int item = threadIdx.x; item < nlanes * NB; item += BLOCK) {
+    const int lane = item / NB;
+    const int bidx = item - lane * NB;
+    cpx<T>* Zl = Z + lane * PL;
     const int j = bidx & (e - 1);
     const int base = ((bidx >> (logL - 3)) << logL) + j;
     cpx<T> x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = Z[pidx<T>(base + q * e)];
+    for (int q = 0; q < 8; ++q) x[q] = Zl[pidx<T>(base + q * e)];
     if (!DIF && j) {
 #pragma unroll
       for (int q = 1; q < 8; ++q) x[q] = x[q] * tw[(q - 1) * e + j];
@@ -201,7 +204,7 @@ __device__ __forceinline__ void radix8_stage(cpx<T>* Z0, cpx<T>* Z1, const cpx<T
       for (int q = 1; q < 8; ++q) x[q] = x[q] * conj(tw[(q - 1) * e + j]);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) Z[pidx<T>(base + q * e)] = x[q];
+    for (int q = 0; q < 8; ++q) Zl[pidx<T>(base + q * e)] = x[q];
   }
 }
 
@@ -213,14 +216,20 @@ __device__ __forceinline__ void products(cpx<T>& z0, cpx<T>& z1) {
   z1 = mk<T>(-h * v1, (T)0);
 }
 
-// The fused middle stage (span 2^LOGMID, twiddles all 1): last inverse DFT,
-// products, first forward DFT, on the same positions.
+// The fused middle stage (span 2^LOGMID, twiddles all 1) on `npairs` lane
+// pairs (lanes 2p and 2p+1 hold one state): last inverse DFT, products, first
+// forward DFT, on the same positions.
 template <typename T, int LOGN, int BLOCK>
-__device__ __forceinline__ void middle_stage(cpx<T>* Z0, cpx<T>* Z1) {
+__device__ __forceinline__ void middle_stage(cpx<T>* Z, int npairs) {
   constexpr int N = 1 << LOGN;
+  constexpr int PL = padded_len<T>(N);
   constexpr int LOGMID = stage_log_mid(LOGN);
   constexpr int R = 1 << LOGMID;
-  for (int i = threadIdx.x; i < N / R; i += BLOCK) {
+  for (int item = threadIdx.x; item < npairs * (N / R); item += BLOCK) {
+    const int pair = item / (N / R);
+    const int i = item - pair * (N / R);
+    cpx<T>* Z0 = Z + 2 * pair * PL;
+    cpx<T>* Z1 = Z0 + PL;
     cpx<T> a[8], b[8];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -257,22 +266,23 @@ __device__ __forceinline__ void middle_stage(cpx<T>* Z0, cpx<T>* Z1) {
   }
 }
 
-// Inverse transform, products and forward transform of the lanes Z0, Z1
-// (entry and exit synchronised).  TW: the outer stages' twiddle tables.
+// Inverse transform, products and forward transform of `nstates` states whose
+// lane pairs are stored back to back from Z (entry and exit synchronised).
+// TW: the outer stages' twiddle tables.
 template <typename T, int LOGN, int BLOCK>
-__device__ __forceinline__ void nonlinear_transform(cpx<T>* Z0, cpx<T>* Z1, const cpx<T>* TW) {
+__device__ __forceinline__ void nonlinear_transform(cpx<T>* Z, int nstates, const cpx<T>* TW) {
   constexpr int N = 1 << LOGN;
   constexpr int LOGMID = stage_log_mid(LOGN);
 #pragma unroll
   for (int logL = LOGN; logL > LOGMID; logL -= 3) {
-    radix8_stage<T, N, BLOCK, +1, true>(Z0, Z1, TW + twiddle_offset(LOGN, logL), logL);
+    radix8_stage<T, N, BLOCK, +1, true>(Z, 2 * nstates, TW + twiddle_offset(LOGN, logL), logL);
     __syncthreads();
   }
-  middle_stage<T, LOGN, BLOCK>(Z0, Z1);
+  middle_stage<T, LOGN, BLOCK>(Z, nstates);
   __syncthreads();
 #pragma unroll
   for (int logL = LOGMID + 3; logL <= LOGN; logL += 3) {
-    radix8_stage<T, N, BLOCK, -1, false>(Z0, Z1, TW + twiddle_offset(LOGN, logL), logL);
+    radix8_stage<T, N, BLOCK, -1, false>(Z, 2 * nstates, TW + twiddle_offset(LOGN, logL), logL);
     __syncthreads();
   }
 }
