@@ -64,6 +64,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched"], default="headline",
+                    help="headline: the contract line (default); tts: time to 1e-5 relative error against the "
+                         "oracle's serial fine solution, FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
+                         "batched: 1024 uneven instances in one batch vs the FP64 path one instance at a time")
+    ap.add_argument("--instances", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -324,10 +329,197 @@ def run_reference(args, rank: int) -> dict | None:
     }
 
 
+# ----------------------------------------------------------------------------- other measurements
+
+def _parseval(a):
+    import numpy as np
+    wgt = np.full(a.shape[-1], 2.0)
+    wgt[0] = 1.0
+    return np.sqrt(np.sum(wgt * np.abs(a) ** 2, axis=(-2, -1)))
+
+
+def run_tts(args) -> dict:
+    """Time to the first parareal iterate within 1e-5 (max over slices of the relative
+    L2 error) of the serial fine solution computed by the FP64 oracle, for the FP32-bulk
+    and the plain FP64 path, one instance each, end to end through the C ABI with host
+    buffers (u0 in; predictor and iterations; all slices out)."""
+    import numpy as np
+    import torch
+
+    from oracle import rsw as o
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    w = WORKLOAD
+    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+    t0 = time.perf_counter()
+    ref = o.serial_fine(w.initial_state(), p, w.slices)
+    t_ref = time.perf_counter() - t0
+    H = w.n_grid // 2 + 1
+    out = {"mode": "tts", "workload": w.name, "target": 1e-5, "reference": "FP64 oracle serial fine solution",
+           "reference_seconds": t_ref}
+    u0h = torch.from_numpy(w.initial_state()).pin_memory()
+    Uh = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128).pin_memory()
+    kcap = 8
+    for name, prec in (("fp64", b.ARP_FP64), ("fp32", b.ARP_FP32)):
+        with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
+            errs, kstar = [], None
+            b.arp_set_initial(s.ctx, u0h)
+            for k in range(kcap + 1):
+                b.arp_parareal_iterate(s.ctx)
+                b.arp_get_slices(s.ctx, Uh)
+                e = float(np.max(_parseval(Uh.numpy()[1:] - ref[1:]) / _parseval(ref[1:])))
+                errs.append(e)
+                if e <= 1e-5 and kstar is None:
+                    kstar = k
+                    break
+            times = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                b.arp_set_initial(s.ctx, u0h)
+                for _k in range((kstar if kstar is not None else kcap) + 1):
+                    b.arp_parareal_iterate(s.ctx)
+                b.arp_get_slices(s.ctx, Uh)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+        out[name] = {"k_star": kstar, "errors_per_k": errs, "seconds": min(times)}
+    if out["fp64"]["k_star"] is not None and out["fp32"]["k_star"] is not None:
+        out["speedup_fp32_vs_fp64"] = out["fp64"]["seconds"] / out["fp32"]["seconds"]
+    return out
+
+
+def run_precision(args) -> dict:
+    """Precision sweep on the N=1024 instance (eps=1e-4, 512 slices, 1954 fine steps,
+    M=128): per-field relative L2 error of one fine sweep against the oracle and the
+    mean-height drift, for FP64 and FP32 bulk; then full-size parareal, FP32 against FP64
+    (iterates k = 0..3) and the time per iteration of each."""
+    import numpy as np
+    import torch
+
+    from oracle import rsw as o
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    w = ri.SWEEP_N1024
+    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+    H = w.n_grid // 2 + 1
+    x = ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, 3, 500) * 64.0
+    ref = o.fine_propagate(x, p)
+    out = {"mode": "precision", "workload": w.name, "fine_sweep_vs_oracle": {}, "parareal_fp32_vs_fp64": {}}
+    fields = ("v1", "v2", "h")
+    iterates = {}
+    for name, prec in (("fp64", b.ARP_FP64), ("fp32", b.ARP_FP32)):
+        with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
+            xin = torch.from_numpy(x).cuda()
+            y = torch.empty_like(xin)
+            b.arp_fine_batch(s.ctx, xin, y)
+            got = y.cpu().numpy()
+            rel = {f: float(np.max(np.linalg.norm(got[:, i] - ref[:, i], axis=-1) / np.linalg.norm(ref[:, i], axis=-1)))
+                   for i, f in enumerate(fields)}
+            drift = float(np.max(np.abs(got[:, 2, 0] - x[:, 2, 0].real) / np.abs(x[:, 2, 0].real)))
+            out["fine_sweep_vs_oracle"][name] = {"rel_l2": rel, "mean_height_drift": drift}
+            b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+            U = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
+            its, ms = [], []
+            for k in range(4):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                b.arp_parareal_iterate(s.ctx)
+                torch.cuda.synchronize()
+                ms.append(1e3 * (time.perf_counter() - t0))
+                b.arp_get_slices(s.ctx, U)
+                its.append(U.cpu().numpy())
+            iterates[name] = its
+            out["parareal_fp32_vs_fp64"][name + "_ms_per_iteration"] = ms[1:]
+    d = []
+    for k in range(4):
+        a, r = iterates["fp32"][k][1:], iterates["fp64"][k][1:]
+        d.append(float(np.max(_parseval(a - r) / _parseval(r))))
+    out["parareal_fp32_vs_fp64"]["max_rel_l2_per_k"] = d
+    h0 = w.initial_state()[2, 0].real
+    out["parareal_fp32_vs_fp64"]["mean_height_drift_fp32"] = float(
+        np.max(np.abs(iterates["fp32"][3][:, 2, 0].real - h0)) / abs(h0))
+    return out
+
+
+def run_batched(args) -> dict:
+    """Batched uneven instances: `--instances` independent problems (N from
+    {64..1024}, eps log-uniform in [1e-4, 1e-2], 32/64/128 slices, M = 32, T = 1,
+    dt = eps/10) advanced together by arp_batch_iterate in FP32 bulk (predictor +
+    5 iterations), against the plain FP64 path run one instance at a time on a
+    seeded sample of 16 of them."""
+    import numpy as np
+    import torch
+
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    insts = ri.uneven_instances(args.instances)
+    units = [w.slices * w.n_grid * fine_steps(w.dT, w.dt) for w in insts]
+    t0 = time.perf_counter()
+    solvers = [b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=b.ARP_FP32) for w in insts]
+    for s, w in zip(solvers, insts):
+        b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    batch = b.arp_batch_create([s.ctx for s in solvers])
+    levels = 6
+    ms = []
+    for k in range(levels):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lv, ch = b.arp_batch_iterate(batch, len(solvers))
+        ms.append(1e3 * (time.perf_counter() - t0))
+    iter_ms = ms[1:]
+    value = sum(units) / (statistics.mean(iter_ms) / 1e3)
+    # sample: the plain FP64 path, one instance at a time
+    rng = np.random.default_rng(7)
+    sample = sorted(rng.choice(len(insts), size=min(16, len(insts)), replace=False).tolist())
+    t_single, dev = 0.0, 0.0
+    for i in sample:
+        w = insts[i]
+        H = w.n_grid // 2 + 1
+        with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+            for _ in range(levels):
+                b.arp_parareal_iterate(s.ctx)
+            torch.cuda.synchronize()
+            t_single += time.perf_counter() - t0
+            U64 = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
+            b.arp_get_slices(s.ctx, U64)
+        U32 = torch.empty_like(U64)
+        b.arp_get_slices(solvers[i].ctx, U32)
+        a, r = U32.cpu().numpy()[1:], U64.cpu().numpy()[1:]
+        dev = max(dev, float(np.max(_parseval(a - r) / _parseval(r))))
+    b.arp_batch_destroy(batch)
+    for s in solvers:
+        s.close()
+    batch_total_s = sum(ms) / 1e3
+    return {"mode": "batched", "instances": len(insts), "precision": "fp32 bulk, fp64 correction/norm/phases",
+            "value": value, "unit": "fine grid-pt-steps/s", "ms_per_batched_iteration": iter_ms,
+            "predictor_ms": ms[0], "setup_seconds": t_setup, "levels": levels,
+            "batched_seconds_all_levels": batch_total_s,
+            "fp64_single_sample": {"instances": len(sample), "seconds_all_levels": t_single,
+                                   "extrapolated_seconds_all_instances": t_single * len(insts) / len(sample)},
+            "speedup_vs_fp64_one_at_a_time": (t_single * len(insts) / len(sample)) / batch_total_s,
+            "max_rel_l2_fp32_batched_vs_fp64_single": dev,
+            "final_max_change": float(np.nanmax(np.array(ch)))}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.mode != "headline":
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            res = {"tts": run_tts, "precision": run_precision, "batched": run_batched}[args.mode](args)
+            print(json.dumps(res), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank)
         if out is not None:

@@ -198,6 +198,31 @@ const char* arp_last_error(const arp_ctx* ctx);
 arp_status arp_coarse_avg_static(int N, double eps, double dT, int M, const double* U_in, double* Nbar_out,
                                  int batch, void* stream);
 
+/*
+ * Batches: one parareal iteration of many independent problems at once.
+ * arp_batch_create groups `count` existing contexts (not owned; all on the
+ * current device).  arp_batch_iterate advances every context that has an
+ * initial state by one level, exactly as arp_parareal_iterate would (the
+ * predictor for contexts at their first call), but runs the work of all
+ * contexts of the same grid size and precision in fused launches: one fine
+ * sweep over every (problem, slice), one correction, one launch of one
+ * thread-block cluster per problem for the serial chains (a context whose
+ * chain cannot run as a cluster gets its own chain launch), and one norm over
+ * all slices.  The blocks run the same kernel bodies as the single-problem
+ * path, so each problem's iterates do not depend on the other members.
+ * levels[i] / changes[i] (arrays of `count`, may be NULL) receive context i's
+ * level and relative change (+inf after its predictor, NaN if it has no
+ * initial state).  Synchronises `stream`.  A context of a batch must not be
+ * used by another call while arp_batch_iterate runs.  On ARP_ETIMEOUT or
+ * ARP_ENONFINITE the other problems have still advanced; the failing
+ * context's arp_last_error tells what happened.
+ */
+typedef struct arp_batch arp_batch;
+arp_status arp_batch_create(arp_batch** out, arp_ctx* const* ctxs, int count);
+arp_status arp_batch_iterate(arp_batch* batch, void* stream, int* levels, double* changes);
+arp_status arp_batch_destroy(arp_batch* batch);
+const char* arp_batch_last_error(const arp_batch* batch);
+
 /* arp_info: sizes of a context: out[0]=N, out[1]=H, out[2]=K, out[3]=slices,
  * out[4]=M, out[5]=fine steps per slice, out[6]=current level k (-1 before the
  * predictor), out[7]=precision. */

@@ -45,6 +45,10 @@ _SIGS = {
     "arp_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "arp_coarse_avg_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P,
                                              _P, ctypes.c_int, _P]),
+    "arp_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
+    "arp_batch_iterate": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "arp_batch_destroy": (ctypes.c_int, [_P]),
+    "arp_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -194,6 +198,38 @@ def arp_destroy(ctx: int) -> None:
 
 def arp_last_error(ctx: Optional[int]) -> str:
     msg = load_library().arp_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def arp_batch_create(ctxs) -> int:
+    lib = load_library()
+    arr = (_P * len(ctxs))(*ctxs)
+    h = _P()
+    st = lib.arp_batch_create(ctypes.byref(h), arr, len(ctxs))
+    if st != ARP_OK:
+        raise ArpError(st, "arp_batch_create failed")
+    return h.value
+
+
+def arp_batch_iterate(batch: int, count: int, stream=None) -> tuple[list, list]:
+    """One level for every context of the batch; returns (levels, changes)."""
+    lib = load_library()
+    lv = (ctypes.c_int * count)()
+    ch = (ctypes.c_double * count)()
+    st = lib.arp_batch_iterate(batch, _stream(stream), lv, ch)
+    if st != ARP_OK:
+        msg = lib.arp_batch_last_error(batch)
+        raise ArpError(st, msg.decode() if msg else "")
+    return list(lv), list(ch)
+
+
+def arp_batch_destroy(batch: int) -> None:
+    if batch:
+        load_library().arp_batch_destroy(batch)
+
+
+def arp_batch_last_error(batch: int) -> str:
+    msg = load_library().arp_batch_last_error(batch)
     return msg.decode() if msg else ""
 
 

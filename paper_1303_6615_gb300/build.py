@@ -20,7 +20,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libarp.so")
 
 SOURCES = ["api.cu", "tables.cu", "fine64.cu", "fine32.cu", "chain64.cu", "chain32.cu", "coarse.cu",
-           "parareal.cu", "static_avg.cu"]
+           "parareal.cu", "static_avg.cu",
+           "batch.cu", "batch64.cu", "batch32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -20,6 +20,11 @@ arp_status check_cuda(arp_ctx* c, cudaError_t e, const char* what) {
               std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+arp_status ensure_tables(arp_ctx* c, cudaStream_t s) {
+  if (!c->tables_dirty) return ARP_OK;
+  return build_tables(c, s);
+}
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -36,14 +41,25 @@ struct Sizes {
   size_t tables, work, state;
 };
 
+// States per pass of the batched time average: all slices, but at most what a
+// 8 MiB partial-sum workspace holds (at least one); the parareal path does
+// not use this workspace.
+int coarse_chunk(int slices, size_t P, size_t K1) {
+  const size_t per = P * 3 * K1 * 16;
+  size_t c = ((size_t)8 << 20) / per;
+  if (c < 1) c = 1;
+  return (int)(c < (size_t)slices ? c : (size_t)slices);
+}
+
 Sizes sizes_of(int N, int slices, int M) {
   const size_t H = N / 2 + 1, K1 = (N - 1) / 3 + 1, S = slices;
   const size_t qc = (M + kMaxNodeBlocks - 1) / kMaxNodeBlocks;
   const size_t P = (M + qc - 1) / qc;
+  const size_t CC = coarse_chunk(slices, P, K1);
   Sizes z;
   z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (size_t)N * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
              (size_t)M * 12 + K1 * 8 + 3 * K1 * 16;
-  z.work = 2 * S * 3 * K1 * 16 + (S + 1) * P * 3 * K1 * 16 + (S + 1) * 8 + 16 + 16;
+  z.work = 2 * CC * 3 * K1 * 16 + (CC + 1) * P * 3 * K1 * 16 + (S + 1) * 8 + 16 + 16;
   z.state = 2 * (S + 1) * 3 * H * 16 + 3 * S * 3 * H * 16;
   return z;
 }
@@ -71,7 +87,7 @@ void release(arp_ctx* c) {
 }
 
 arp_status allocate(arp_ctx* c) {
-  const size_t K1 = c->K1, H = c->H, S = c->slices, M = c->M, P = c->P, N = c->N;
+  const size_t K1 = c->K1, H = c->H, S = c->slices, M = c->M, P = c->P, N = c->N, CC = c->cchunk;
   arp_status r;
 #define ARP_ALLOC(ptr, bytes) \
   if ((r = alloc(c, &(ptr), (bytes))) != ARP_OK) return r;
@@ -90,9 +106,9 @@ arp_status allocate(arp_ctx* c) {
   ARP_ALLOC(c->weight32, M * 4);
   ARP_ALLOC(c->dhalf, K1 * 8);
   ARP_ALLOC(c->gphase, 3 * K1 * 16);
-  ARP_ALLOC(c->W, S * 3 * K1 * 16);
-  ARP_ALLOC(c->W2, S * 3 * K1 * 16);
-  ARP_ALLOC(c->partial, S * P * 3 * K1 * 16);
+  ARP_ALLOC(c->W, CC * 3 * K1 * 16);
+  ARP_ALLOC(c->W2, CC * 3 * K1 * 16);
+  ARP_ALLOC(c->partial, CC * P * 3 * K1 * 16);
   ARP_ALLOC(c->rel, (S + 1) * 8);
   ARP_ALLOC(c->scalar, 16);
   ARP_ALLOC(c->sync, 16);
@@ -117,11 +133,6 @@ bool is_host_pointer(const void* p) {
     return true;
   }
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
-}
-
-arp_status ensure_tables(arp_ctx* c, cudaStream_t s) {
-  if (!c->tables_dirty) return ARP_OK;
-  return build_tables(c, s);
 }
 
 // Projects one state onto the state space in place: bins above K zero, k = 0 real.
@@ -176,6 +187,7 @@ arp_status arp_create(arp_ctx** out, int N, double eps, double nu, int slices, d
   c->M = M;
   c->qc = (M + kMaxNodeBlocks - 1) / kMaxNodeBlocks;
   c->P = (M + c->qc - 1) / c->qc;
+  c->cchunk = coarse_chunk(slices, c->P, c->K1);
   c->eps = eps;
   c->nu = nu;
   c->dT = dT;

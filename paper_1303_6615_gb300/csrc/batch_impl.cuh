@@ -1,0 +1,110 @@
+// batch_impl.cuh -- fused launches over many independent problems (contexts of
+// the same grid size and precision): the fine sweep of every (problem, slice)
+// pair in one launch, and the serial coarse chains of all problems in one
+// launch of one thread-block cluster per problem.  The blocks run the same
+// device bodies as the single-problem kernels, so a problem's results do not
+// depend on which other problems share the launch.
+#pragma once
+
+#include <type_traits>
+
+#include "cluster_chain.cuh"
+
+namespace arp {
+
+template <typename T>
+struct FineJob {
+  const cd* in;   // [slices][3][H]
+  cd* out;        // [slices][3][H]
+  int steps;
+  FineTabs<T> tb;
+};
+
+template <typename T>
+struct ChainJob {
+  ClusterChainArgs a;
+  NbarTabs<T> tb;
+};
+
+// Index of the job owning block b: the last i with first[i] <= b (first ascending).
+__device__ __forceinline__ int find_job(const int* __restrict__ first, int njobs, int b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fine_batch_kernel(const FineJob<T>* __restrict__ jobs,
+                                                           const int* __restrict__ first, int njobs) {
+  const int i = find_job(first, njobs, blockIdx.x);
+  const FineJob<T> j = jobs[i];
+  if constexpr (std::is_same<T, float>::value)
+    fine_f32_body<LOGN, BLOCK>(j.in, j.out, j.steps, j.tb, blockIdx.x - first[i]);
+  else
+    fine_body<T, LOGN, BLOCK>(j.in, j.out, j.steps, j.tb, blockIdx.x - first[i]);
+}
+
+template <typename T, int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) chain_batch_kernel(const ChainJob<T>* __restrict__ jobs) {
+  const int i = blockIdx.x / cooperative_groups::this_cluster().num_blocks();
+  const ChainJob<T> j = jobs[i];
+  chain_cluster_body<T, LOGN, BLOCK>(j.a, j.tb);
+}
+
+template <typename T, int LOGN>
+arp_status launch_fine_batch_n(arp_ctx* err, const void* jobs, const int* first, int njobs, int nblocks,
+                               cudaStream_t s) {
+  constexpr int BLOCK = FineBlock<LOGN>::value;
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK>::kBytes : FineLayout<T, LOGN>::kBytes;
+  const void* kern = (const void*)fine_batch_kernel<T, LOGN, BLOCK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return check_cuda(err, e, "batch fine: shared-memory attribute");
+  void* args[] = {(void*)&jobs, (void*)&first, &njobs};
+  return check_cuda(err, cudaLaunchKernel(kern, dim3(nblocks), dim3(BLOCK), args, smem, s), "batch fine: launch");
+}
+
+// Cluster chains of `count` problems of one grid size; `plans` gets each
+// problem's plan for the chosen cluster size.  ARP_EINVAL (nothing launched)
+// if some problem has no cluster plan.
+template <typename T, int LOGN>
+arp_status plan_chain_batch_n(const int* M, const int* K1, int count, int* C_out, ClusterPlan* plans,
+                              size_t* smem_out) {
+  constexpr int BLOCK = ClusterBlock<LOGN>::value;
+  const void* kern = (const void*)chain_batch_kernel<T, LOGN, BLOCK>;
+  for (int C : {16, 8}) {
+    size_t smem = 0;
+    bool ok = true;
+    for (int i = 0; i < count && ok; ++i) {
+      plans[i] = cluster_plan<T>(LOGN, M[i], K1[i], C);
+      ok = plans[i].smem <= kMaxSmem;
+      smem = plans[i].smem > smem ? plans[i].smem : smem;
+    }
+    if (!ok) continue;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    if (!cluster_config(kern, C, BLOCK, smem, count, nullptr, &cfg, attr)) continue;
+    *C_out = C;
+    *smem_out = smem;
+    return ARP_OK;
+  }
+  return ARP_EINVAL;
+}
+
+template <typename T, int LOGN>
+arp_status launch_chain_batch_n(arp_ctx* err, const void* jobs, int count, int C, size_t smem, cudaStream_t s) {
+  constexpr int BLOCK = ClusterBlock<LOGN>::value;
+  const void* kern = (const void*)chain_batch_kernel<T, LOGN, BLOCK>;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  if (!cluster_config(kern, C, BLOCK, smem, count, s, &cfg, attr))
+    return fail(err, ARP_EINVAL, "batch chain: cluster configuration not available");
+  void* args[] = {(void*)&jobs};
+  return check_cuda(err, cudaLaunchKernelExC(&cfg, kern, args), "batch chain: launch");
+}
+
+}  // namespace arp

@@ -59,7 +59,7 @@ inline size_t cluster_chain_smem_bytes(int logn, int q, int own, int C, bool ph_
 }
 
 template <typename T, int LOGN, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) chain_cluster_kernel(ClusterChainArgs a, NbarTabs<T> tb) {
+__device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, const NbarTabs<T>& tb) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   constexpr int N = 1 << LOGN;
@@ -249,6 +249,65 @@ __global__ void __launch_bounds__(BLOCK) chain_cluster_kernel(ClusterChainArgs a
   cl.sync();  // no CTA leaves while another may still store into its shared memory
 }
 
+template <typename T, int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) chain_cluster_kernel(ClusterChainArgs a, NbarTabs<T> tb) {
+  chain_cluster_body<T, LOGN, BLOCK>(a, tb);
+}
+
+// Shared-memory plan of the cluster chain for one instance with C CTAs: stage
+// what fits (the per-node terms first, for balance, then the node phases).
+struct ClusterPlan {
+  int q, own, ph_smem, tmp_smem;
+  size_t smem;  // > kMaxSmem if it does not fit at all
+};
+constexpr size_t kMaxSmem = 227 * 1024;
+
+template <typename T>
+inline ClusterPlan cluster_plan(int logn, int M, int K1, int C) {
+  ClusterPlan p{(M + C - 1) / C, (K1 + C - 1) / C, 1, 1, 0};
+  p.smem = cluster_chain_smem_bytes<T>(logn, p.q, p.own, C, true, true);
+  if (p.smem > kMaxSmem) {
+    p.ph_smem = 0;
+    p.smem = cluster_chain_smem_bytes<T>(logn, p.q, p.own, C, false, true);
+  }
+  if (p.smem > kMaxSmem) {
+    p.tmp_smem = 0;
+    p.smem = cluster_chain_smem_bytes<T>(logn, p.q, p.own, C, false, false);
+  }
+  return p;
+}
+
+// Launch configuration of `count` clusters of C CTAs of `kern`; true if at
+// least one such cluster can be resident.
+inline bool cluster_config(const void* kern, int C, int block, size_t smem, int count, cudaStream_t s,
+                           cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+  if (smem > kMaxSmem) return false;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  *cfg = cudaLaunchConfig_t{};
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->gridDim = dim3(C * count);
+  cfg->blockDim = dim3(block);
+  cfg->dynamicSmemBytes = smem;
+  cfg->stream = s;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  int clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&clusters, kern, cfg);
+  if (e != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 // Launches the cluster chain; ARP_EINVAL (nothing launched) if no cluster of 16
 // or 8 CTAs with this kernel's shared memory can be scheduled.
 template <typename T, int LOGN>
@@ -256,50 +315,15 @@ arp_status launch_cluster_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaSt
   constexpr int BLOCK = ClusterBlock<LOGN>::value;
   const void* kern = (const void*)chain_cluster_kernel<T, LOGN, BLOCK>;
   for (int C : {16, 8}) {
-    const int q = (c->M + C - 1) / C;
-    const int own = (c->K1 + C - 1) / C;
-    // stage what fits: the per-node terms first (balance), then the node phases
-    bool tmp_smem = true, ph_smem = true;
-    size_t smem = cluster_chain_smem_bytes<T>(LOGN, q, own, C, ph_smem, tmp_smem);
-    if (smem > 227 * 1024) {
-      ph_smem = false;
-      smem = cluster_chain_smem_bytes<T>(LOGN, q, own, C, ph_smem, tmp_smem);
-    }
-    if (smem > 227 * 1024) {
-      tmp_smem = false;
-      smem = cluster_chain_smem_bytes<T>(LOGN, q, own, C, ph_smem, tmp_smem);
-    }
-    if (smem > 227 * 1024) continue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    cudaLaunchConfig_t cfg = {};
+    const ClusterPlan p = cluster_plan<T>(LOGN, c->M, c->K1, C);
+    cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(BLOCK);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
-    if (e != cudaSuccess || clusters < 1) {
-      cudaGetLastError();
-      continue;
-    }
-    ClusterChainArgs a{V, U, Gc, c->slices, c->M, q, own, ph_smem ? 1 : 0, tmp_smem ? 1 : 0, c->dT, c->inv_sig64,
+    if (!cluster_config(kern, C, BLOCK, p.smem, 1, s, &cfg, attr)) continue;
+    ClusterChainArgs a{V, U, Gc, c->slices, c->M, p.q, p.own, p.ph_smem, p.tmp_smem, c->dT, c->inv_sig64,
                        c->sk_sig64, c->dhalf, c->gphase};
     NbarTabs<T> tb = nbar_tabs<T>(c);
     void* args[] = {&a, &tb};
-    e = cudaLaunchKernelExC(&cfg, kern, args);
-    return check_cuda(c, e, "cluster chain: launch");
+    return check_cuda(c, cudaLaunchKernelExC(&cfg, kern, args), "cluster chain: launch");
   }
   return fail(c, ARP_EINVAL, "cluster chain: no cluster of 16 or 8 blocks fits");
 }

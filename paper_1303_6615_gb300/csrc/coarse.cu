@@ -107,8 +107,8 @@ arp_status launch_nbar_reduce(arp_ctx* c, int mode, const cd* partial, const cd*
 }
 
 arp_status coarse_avg(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
-  for (int b0 = 0; b0 < batch; b0 += c->slices) {
-    const int nb = batch - b0 < c->slices ? batch - b0 : c->slices;
+  for (int b0 = 0; b0 < batch; b0 += c->cchunk) {
+    const int nb = batch - b0 < c->cchunk ? batch - b0 : c->cchunk;
     const size_t off = (size_t)b0 * 3 * c->H;
     arp_status r;
     if ((r = launch_to_eigen(c, in + off, c->W, nb, false, s)) != ARP_OK) return r;
@@ -121,8 +121,8 @@ arp_status coarse_avg(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t
 }
 
 arp_status coarse_step(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
-  for (int b0 = 0; b0 < batch; b0 += c->slices) {
-    const int nb = batch - b0 < c->slices ? batch - b0 : c->slices;
+  for (int b0 = 0; b0 < batch; b0 += c->cchunk) {
+    const int nb = batch - b0 < c->cchunk ? batch - b0 : c->cchunk;
     const size_t off = (size_t)b0 * 3 * c->H;
     arp_status r;
     if ((r = launch_to_eigen(c, in + off, c->W, nb, true, s)) != ARP_OK) return r;

@@ -14,6 +14,7 @@ struct arp_ctx {
   int N = 0, logN = 0, H = 0, K = 0, K1 = 0;
   int slices = 0, M = 0, steps = 0;
   int qc = 1, P = 0;             // nodes per block, node chunks P = ceil(M / qc)
+  int cchunk = 1;                // states per pass of arp_coarse_avg / arp_coarse_step
   double eps = 0, nu = 0, dT = 0, dt = 0, h = 0;
   double T0 = 0, F = 1.0, tol = 0.0;
   bool T0_set = false;
@@ -39,10 +40,10 @@ struct arp_ctx {
   double* dhalf = nullptr;       // [K1] e^{-nu k^4 dT/2}
   arp::cd* gphase = nullptr;     // [3][K1] e^{-i omega dT/eps}
 
-  // workspaces (sized for `slices` states)
-  arp::cd* W = nullptr;          // [slices][3][K1] eigen, FP64
-  arp::cd* W2 = nullptr;         // [slices][3][K1]
-  arp::cd* partial = nullptr;    // [slices][P][3][K1]
+  // workspaces (sized for `cchunk` states)
+  arp::cd* W = nullptr;          // [cchunk][3][K1] eigen, FP64
+  arp::cd* W2 = nullptr;         // [cchunk][3][K1]
+  arp::cd* partial = nullptr;    // [cchunk][P][3][K1]
   double* rel = nullptr;         // [slices + 1] per-slice relative change
   double* scalar = nullptr;      // [2]: max relative change
   unsigned* sync = nullptr;      // [4]: [0] grid-barrier counter, [1] status (0 ok, else an arp_status)
@@ -68,8 +69,9 @@ namespace arp {
 arp_status fail(arp_ctx* c, arp_status s, const std::string& msg);
 arp_status check_cuda(arp_ctx* c, cudaError_t e, const char* what);
 
-// tables.cu
+// tables.cu (build) and api.cu (rebuild when options changed them)
 arp_status build_tables(arp_ctx* c, cudaStream_t s);
+arp_status ensure_tables(arp_ctx* c, cudaStream_t s);
 
 // fine.cu: F applied to `batch` physical states.
 arp_status launch_fine(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
@@ -100,5 +102,7 @@ arp_status launch_cluster_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStre
 
 // parareal.cu
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);
+// The serial chain of one context (cluster, else cooperative grid, else launches).
+arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s);
 
 }  // namespace arp

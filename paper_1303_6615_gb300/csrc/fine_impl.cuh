@@ -99,8 +99,8 @@ __device__ __forceinline__ void store_phys64(cd* __restrict__ dst, int H, int k,
 }
 
 template <typename T, int LOGN, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict__ in, cd* __restrict__ out,
-                                                           int steps, FineTabs<T> tb) {
+__device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
+                                          const FineTabs<T>& tb, int slice) {
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
   constexpr int K = (N - 1) / 3;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
   T* IS = reinterpret_cast<T*>(ACC + 3 * K1 + (kPair ? 6 * K1 : 0));
   T* SS = IS + K1;
 
-  const cd* src = in + (size_t)blockIdx.x * 3 * H;
+  const cd* src = in + (size_t)slice * 3 * H;
   if (kTwShared)
     for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TWs[t] = tb.tw[t];
   for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
     }
   }
 
-  cd* dst = out + (size_t)blockIdx.x * 3 * H;
+  cd* dst = out + (size_t)slice * 3 * H;
   for (int k = threadIdx.x; k < H; k += BLOCK) {
     if (k <= K) {
       cd a[3];
@@ -234,6 +234,12 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
   }
 }
 
+template <typename T, int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict__ in, cd* __restrict__ out,
+                                                           int steps, FineTabs<T> tb) {
+  fine_body<T, LOGN, BLOCK>(in, out, steps, tb, blockIdx.x);
+}
+
 // FP32 fine sweep with the ETDRK4 state in registers: thread t owns the
 // wavenumbers k = t + r BLOCK (r < MPT), holding u (float pair), N(u), a1 and
 // the update sum (float pair) for the three branches; shared memory holds only
@@ -246,8 +252,8 @@ struct F32Layout {
 };
 
 template <int LOGN, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
-                                                               int steps, FineTabs<float> tb) {
+__device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
+                                              const FineTabs<float>& tb, int slice) {
   using T = float;
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restr
   T* SS = IS + K1;
 
   cf u[MPT][3], ulo[MPT][3], nu[MPT][3], a1[MPT][3], acc[MPT][3], acclo[MPT][3];
-  const cd* src = in + (size_t)blockIdx.x * 3 * H;
+  const cd* src = in + (size_t)slice * 3 * H;
   for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TW[t] = tb.tw[t];
 #pragma unroll
   for (int r = 0; r < MPT; ++r) {
@@ -334,7 +340,7 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restr
     }
   }
 
-  cd* dst = out + (size_t)blockIdx.x * 3 * H;
+  cd* dst = out + (size_t)slice * 3 * H;
 #pragma unroll
   for (int r = 0; r < MPT; ++r) {
     const int k = threadIdx.x + r * BLOCK;
@@ -348,6 +354,12 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restr
 #pragma unroll
     for (int f = 0; f < 3; ++f) dst[f * H + k] = {0.0, 0.0};
   }
+}
+
+template <int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
+                                                               int steps, FineTabs<float> tb) {
+  fine_f32_body<LOGN, BLOCK>(in, out, steps, tb, blockIdx.x);
 }
 
 template <typename T>

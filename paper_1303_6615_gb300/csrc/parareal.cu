@@ -10,73 +10,28 @@
 #include <cmath>
 
 #include "context.h"
+#include "parareal_kernels.cuh"
 
 namespace arp {
-namespace {
 
-// V = F - G over n elements (complex FP64).
 __global__ void correction_kernel(const cd* __restrict__ f, const cd* __restrict__ g, cd* __restrict__ v, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = f[i] - g[i];
 }
 
-// One block (256 threads) per slice n = 1..S: rel[n] = ||U_n - Uold_n|| / ||U_n||.
 __global__ void slice_change_kernel(const cd* __restrict__ U, const cd* __restrict__ Uold, double* __restrict__ rel,
                                     int H) {
-  __shared__ double sd[256], sn[256];
   const int n = blockIdx.x + 1;
-  const size_t base = (size_t)n * 3 * H;
-  double d = 0.0, nn = 0.0;
-  for (int i = threadIdx.x; i < 3 * H; i += 256) {
-    const int k = i % H;
-    const double w = (k == 0) ? 1.0 : 2.0;
-    const cd a = U[base + i], b = Uold[base + i];
-    const double dx = a.x - b.x, dy = a.y - b.y;
-    d += w * (dx * dx + dy * dy);
-    nn += w * (a.x * a.x + a.y * a.y);
-  }
-  sd[threadIdx.x] = d;
-  sn[threadIdx.x] = nn;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      sd[threadIdx.x] += sd[threadIdx.x + w];
-      sn[threadIdx.x] += sn[threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double dd = sd[0], ns = sn[0];
-    double r;
-    if (ns > 0.0) r = sqrt(dd) / sqrt(ns);
-    else r = (dd > 0.0) ? INFINITY : 0.0;
-    rel[n] = r;
-  }
+  const double r = slice_change_body(U + (size_t)n * 3 * H, Uold + (size_t)n * 3 * H, H);
+  if (threadIdx.x == 0) rel[n] = r;
 }
 
-// One block: out[0] = max_n rel[n] (NaN if any entry is NaN).
 __global__ void max_kernel(const double* __restrict__ rel, int S, double* __restrict__ out) {
-  __shared__ double sm[256];
-  __shared__ int bad[256];
-  double m = 0.0;
-  int nan = 0;
-  for (int n = 1 + threadIdx.x; n <= S; n += 256) {
-    const double r = rel[n];
-    if (r != r) nan = 1;
-    else m = fmax(m, r);
-  }
-  sm[threadIdx.x] = m;
-  bad[threadIdx.x] = nan;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
-      bad[threadIdx.x] |= bad[threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[0] = bad[0] ? NAN : sm[0];
+  const double m = max_change_body(rel, S);
+  if (threadIdx.x == 0) out[0] = m;
 }
+
+namespace {
 
 // G(U_n) for the single state at U + n, written to g_out; u_next = g (+ v), with
 // one launch per step of the link (used when the persistent chain cannot be
@@ -90,6 +45,14 @@ arp_status chain_link(arp_ctx* c, const cd* u, cd* g_out, cd* u_next, const cd* 
   if ((r = launch_nbar_partial(c, c->W2, c->partial, 1, s)) != ARP_OK) return r;
   return launch_nbar_reduce(c, kReduceFinal, c->partial, c->W, nullptr, g_out, v, u_next, 1, s);
 }
+
+// Reads the chain's status word; ARP_ETIMEOUT if a grid barrier gave up.
+arp_status chain_status(arp_ctx* c, unsigned status) {
+  if (status == 0u) return ARP_OK;
+  return fail(c, ARP_ETIMEOUT, "chain: a grid barrier timed out");
+}
+
+}  // namespace
 
 // The whole serial chain n = 0..S-1: one thread-block cluster, else the
 // persistent cooperative kernel, else one link at a time (ARP_OPT_CHAIN
@@ -111,14 +74,6 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
       return r;
   return ARP_OK;
 }
-
-// Reads the chain's status word; ARP_ETIMEOUT if a grid barrier gave up.
-arp_status chain_status(arp_ctx* c, unsigned status) {
-  if (status == 0u) return ARP_OK;
-  return fail(c, ARP_ETIMEOUT, "chain: a grid barrier timed out");
-}
-
-}  // namespace
 
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change) {
   const size_t st = (size_t)3 * c->H;  // complex entries per state

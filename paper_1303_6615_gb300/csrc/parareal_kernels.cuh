@@ -1,0 +1,75 @@
+// parareal_kernels.cuh -- FP64 streaming kernels of the parareal correction
+// and of the stopping quantity, shared by the single-problem driver and by
+// batches (the same reduction order in both, so results do not depend on the
+// batch).
+#pragma once
+
+#include <cmath>
+
+#include "common.cuh"
+
+namespace arp {
+
+// V = F - G over n elements (complex FP64).
+__global__ void correction_kernel(const cd* __restrict__ f, const cd* __restrict__ g, cd* __restrict__ v, size_t n);
+
+// ||U_n - Uold_n||^2 and ||U_n||^2 (Parseval weights 1 at k = 0, 2 above) of the
+// state at `base`, reduced by a 256-thread block in a fixed tree; thread 0
+// returns ||U_n - Uold_n|| / ||U_n|| (0 if both vanish, inf if only ||U_n|| does).
+__device__ __forceinline__ double slice_change_body(const cd* __restrict__ U, const cd* __restrict__ Uold, int H) {
+  __shared__ double sd[256], sn[256];
+  double d = 0.0, nn = 0.0;
+  for (int i = threadIdx.x; i < 3 * H; i += 256) {
+    const int k = i % H;
+    const double w = (k == 0) ? 1.0 : 2.0;
+    const cd a = U[i], b = Uold[i];
+    const double dx = a.x - b.x, dy = a.y - b.y;
+    d += w * (dx * dx + dy * dy);
+    nn += w * (a.x * a.x + a.y * a.y);
+  }
+  sd[threadIdx.x] = d;
+  sn[threadIdx.x] = nn;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sd[threadIdx.x] += sd[threadIdx.x + w];
+      sn[threadIdx.x] += sn[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  const double dd = sd[0], ns = sn[0];
+  if (ns > 0.0) return sqrt(dd) / sqrt(ns);
+  return (dd > 0.0) ? INFINITY : 0.0;
+}
+
+// max of rel[1..S] by a 256-thread block; NaN if any entry is NaN.
+__device__ __forceinline__ double max_change_body(const double* __restrict__ rel, int S) {
+  __shared__ double sm[256];
+  __shared__ int bad[256];
+  double m = 0.0;
+  int nan = 0;
+  for (int n = 1 + threadIdx.x; n <= S; n += 256) {
+    const double r = rel[n];
+    if (r != r) nan = 1;
+    else m = fmax(m, r);
+  }
+  sm[threadIdx.x] = m;
+  bad[threadIdx.x] = nan;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+      bad[threadIdx.x] |= bad[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  return bad[0] ? NAN : sm[0];
+}
+
+// One 256-thread block per slice n = 1..S: rel[n] = ||U_n - Uold_n|| / ||U_n||.
+__global__ void slice_change_kernel(const cd* __restrict__ U, const cd* __restrict__ Uold, double* __restrict__ rel,
+                                    int H);
+// One 256-thread block: out[0] = max_n rel[n].
+__global__ void max_kernel(const double* __restrict__ rel, int S, double* __restrict__ out);
+
+}  // namespace arp

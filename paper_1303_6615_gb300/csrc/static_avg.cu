@@ -106,7 +106,8 @@ extern "C" arp_status arp_coarse_avg_static(int N, double eps, double dT, int M,
   c.gphase = reinterpret_cast<cd*>(carve(sizes[14]));
   c.W = reinterpret_cast<cd*>(carve((size_t)chunk * 3 * K1 * 16));
   c.partial = reinterpret_cast<cd*>(carve((size_t)chunk * P * 3 * K1 * 16));
-  c.slices = chunk;  // states per pass through the workspace
+  c.slices = chunk;
+  c.cchunk = chunk;  // states per pass through the workspace
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   arp_status r = build_tables(&c, s);
