@@ -64,10 +64,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched"], default="headline",
+    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve"], default="headline",
                     help="headline: the contract line (default); tts: time to 1e-5 relative error against the "
                          "oracle's serial fine solution, FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
-                         "batched: 1024 uneven instances in one batch vs the FP64 path one instance at a time")
+                         "batched: 1024 uneven instances in one batch vs the FP64 path one instance at a time; "
+                         "serve: Poisson request streams through the continuous-batching server")
     ap.add_argument("--instances", type=int, default=1024)
     return ap.parse_args()
 
@@ -509,6 +510,74 @@ def run_batched(args) -> dict:
             "final_max_change": float(np.nanmax(np.array(ch)))}
 
 
+def serve_requests(count: int, seed: int):
+    """Seeded serving requests: N from {128..2048}, eps log-uniform in [1e-4, 1e-2],
+    slices from {32..512}, T from {0.1, 0.5, 1}, dt = min(eps/10, T/slices), M = 32, at most 5
+    iterations or a change <= 1e-8; initial spectra as the small workload's (|k| <= 8,
+    scale e^{-k^2/16}), request i seeded seed + i."""
+    from paper_1303_6615_gb300 import serve
+    g = ri.SplitMix64(seed ^ 0x5E7E)
+    out = []
+    for i in range(count):
+        n = (128, 256, 512, 1024, 2048)[g.next_u64() % 5]
+        eps = 10.0 ** (-4.0 + 2.0 * g.uniform())
+        S = (32, 64, 128, 256, 512)[g.next_u64() % 5]
+        T = (0.1, 0.5, 1.0)[g.next_u64() % 3]
+        u0 = ri.random_spectrum(n, 8, 16.0, seed + i)
+        out.append(serve.Request(n, eps, 1e-4, S, T, min(eps / 10.0, T / S), 32, u0, k_max=5, tol=1e-8))
+    return out
+
+
+def run_serve(args) -> dict:
+    """Poisson request streams (rates 10, 100, 1000 per second, 64 requests each)
+    through the continuous-batching FP32 server, against the plain FP64 path
+    serving the same requests one at a time in arrival order (first come first
+    served, each request's FP64 service time measured on its own)."""
+    import numpy as np
+    import torch
+
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    from paper_1303_6615_gb300 import serve
+    bld.build()
+    count = 64
+    base = serve_requests(count, 3000)
+    service64 = []
+    for r in base:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        serve.solve_alone(r, b.ARP_FP64)
+        torch.cuda.synchronize()
+        service64.append(time.perf_counter() - t0)
+    out = {"mode": "serve", "requests_per_rate": count, "fp64_one_at_a_time_service_s_mean": float(np.mean(service64)),
+           "rates": {}}
+    for rate in (10.0, 100.0, 1000.0):
+        rng = np.random.default_rng(int(rate))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        reqs = serve_requests(count, 3000)
+        server = serve.Server(memory_budget=24 << 30, max_active=256, precision=b.ARP_FP32)
+        try:
+            t0 = server.clock()
+            done = serve.replay(server, list(zip(arrivals.tolist(), reqs)))
+            makespan = server.clock() - t0
+        finally:
+            server.close()
+        lat = np.array([r.latency for r in done])
+        # first come first served, one at a time, FP64
+        finish, lat64 = 0.0, []
+        for a, s in zip(arrivals, service64):
+            finish = max(finish, a) + s
+            lat64.append(finish - a)
+        lat64 = np.array(lat64)
+        out["rates"][str(int(rate))] = {
+            "batched_fp32": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                             "throughput_req_s": count / makespan},
+            "fp64_one_at_a_time": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                                   "throughput_req_s": count / (finish - 0.0)},
+        }
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -517,7 +586,7 @@ def main():
         if rank == 0:
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-            res = {"tts": run_tts, "precision": run_precision, "batched": run_batched}[args.mode](args)
+            res = {"tts": run_tts, "precision": run_precision, "batched": run_batched, "serve": run_serve}[args.mode](args)
             print(json.dumps(res), flush=True)
         return
     if args.impl == "reference":

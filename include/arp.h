@@ -201,7 +201,8 @@ arp_status arp_coarse_avg_static(int N, double eps, double dT, int M, const doub
 /*
  * Batches: one parareal iteration of many independent problems at once.
  * arp_batch_create groups `count` existing contexts (not owned; all on the
- * current device).  arp_batch_iterate advances every context that has an
+ * current device); with ctxs == NULL it creates an empty batch with room for
+ * `count` members (see arp_batch_reset).  arp_batch_iterate advances every context that has an
  * initial state by one level, exactly as arp_parareal_iterate would (the
  * predictor for contexts at their first call), but runs the work of all
  * contexts of the same grid size and precision in fused launches: one fine
@@ -220,6 +221,10 @@ arp_status arp_coarse_avg_static(int N, double eps, double dT, int M, const doub
 typedef struct arp_batch arp_batch;
 arp_status arp_batch_create(arp_batch** out, arp_ctx* const* ctxs, int count);
 arp_status arp_batch_iterate(arp_batch* batch, void* stream, int* levels, double* changes);
+/* arp_batch_reset: replace the members (count <= the count given at creation;
+ * 0 empties the batch) without reallocating; a serving loop calls it when
+ * requests join or leave. */
+arp_status arp_batch_reset(arp_batch* batch, arp_ctx* const* ctxs, int count);
 arp_status arp_batch_destroy(arp_batch* batch);
 const char* arp_batch_last_error(const arp_batch* batch);
 

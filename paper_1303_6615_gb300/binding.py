@@ -48,6 +48,7 @@ _SIGS = {
     "arp_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
     "arp_batch_iterate": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "arp_batch_destroy": (ctypes.c_int, [_P]),
+    "arp_batch_reset": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.c_int]),
     "arp_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -201,11 +202,15 @@ def arp_last_error(ctx: Optional[int]) -> str:
     return msg.decode() if msg else ""
 
 
-def arp_batch_create(ctxs) -> int:
+def arp_batch_create(ctxs, capacity: Optional[int] = None) -> int:
+    """A batch of the contexts `ctxs`; ctxs=None with `capacity` gives an empty batch."""
     lib = load_library()
-    arr = (_P * len(ctxs))(*ctxs)
     h = _P()
-    st = lib.arp_batch_create(ctypes.byref(h), arr, len(ctxs))
+    if ctxs is None:
+        st = lib.arp_batch_create(ctypes.byref(h), None, int(capacity))
+    else:
+        arr = (_P * len(ctxs))(*ctxs)
+        st = lib.arp_batch_create(ctypes.byref(h), arr, len(ctxs))
     if st != ARP_OK:
         raise ArpError(st, "arp_batch_create failed")
     return h.value
@@ -221,6 +226,14 @@ def arp_batch_iterate(batch: int, count: int, stream=None) -> tuple[list, list]:
         msg = lib.arp_batch_last_error(batch)
         raise ArpError(st, msg.decode() if msg else "")
     return list(lv), list(ch)
+
+
+def arp_batch_reset(batch: int, ctxs) -> None:
+    lib = load_library()
+    arr = (_P * max(1, len(ctxs)))(*ctxs)
+    st = lib.arp_batch_reset(batch, arr, len(ctxs))
+    if st != ARP_OK:
+        raise ArpError(st, arp_batch_last_error(batch))
 
 
 def arp_batch_destroy(batch: int) -> None:

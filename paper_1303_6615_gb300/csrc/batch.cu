@@ -80,6 +80,7 @@ using namespace arp;
 
 struct arp_batch {
   std::vector<arp_ctx*> ctx;
+  int capacity = 0;                // members the device buffers are sized for
   int device = 0;
   unsigned char* dmem = nullptr;   // device: job arrays, prefix arrays, results
   size_t dbytes = 0;
@@ -125,17 +126,18 @@ extern "C" {
 arp_status arp_batch_create(arp_batch** out, arp_ctx* const* ctxs, int count) {
   if (!out) return ARP_EINVAL;
   *out = nullptr;
-  if (count < 1 || !ctxs) return ARP_EINVAL;
+  if (count < 1) return ARP_EINVAL;
   arp_batch* b = new (std::nothrow) arp_batch();
   if (!b) return ARP_ENOMEM;
   cudaGetDevice(&b->device);
-  for (int i = 0; i < count; ++i) {
+  for (int i = 0; ctxs && i < count; ++i) {
     if (!ctxs[i] || ctxs[i]->device != b->device) {
       delete b;
       return ARP_EINVAL;
     }
     b->ctx.push_back(ctxs[i]);
   }
+  b->capacity = count;
   const Layout L = layout_for(count);
   b->dbytes = L.total;
   if (cudaMalloc((void**)&b->dmem, b->dbytes) != cudaSuccess) {
@@ -144,8 +146,18 @@ arp_status arp_batch_create(arp_batch** out, arp_ctx* const* ctxs, int count) {
     return ARP_ENOMEM;
   }
   b->host.assign(b->dbytes, 0);
-  b->out.assign(count, 0.0);
+  b->out.assign(count, 0.0);  // ctxs == NULL: an empty batch with room for `count` members
   *out = b;
+  return ARP_OK;
+}
+
+arp_status arp_batch_reset(arp_batch* b, arp_ctx* const* ctxs, int count) {
+  if (!b) return ARP_EINVAL;
+  if (count < 0 || count > b->capacity || (count > 0 && !ctxs)) return bfail(b, ARP_EINVAL, "batch: bad member list");
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i] || ctxs[i]->device != b->device) return bfail(b, ARP_EINVAL, "batch: bad member");
+  b->ctx.assign(ctxs, ctxs + count);
+  b->out.assign(count > 0 ? count : 1, 0.0);
   return ARP_OK;
 }
 
@@ -162,7 +174,8 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   if (!b) return ARP_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = (int)b->ctx.size();
-  const Layout L = layout_for(n);
+  if (n == 0) return ARP_OK;
+  const Layout L = layout_for(b->capacity);
   unsigned char* H = b->host.data();
   arp_status r;
   std::vector<int> act, iter;  // indices: contexts with an initial state; those past their predictor
