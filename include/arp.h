@@ -70,6 +70,10 @@ typedef enum {
                               else a cooperative grid with bounded grid barriers, else one
                               launch per step), 1 = cooperative grid, 2 = launches; all give
                               the same result up to rounding (default 0) */
+  ARP_OPT_FINE_BLOCK = 7,  /* FP32 fine sweep threads per slice: 0 = the default for the grid
+                              size (the faster on GB300), 1 = N/4, 2 = N/2 (both at least 32,
+                              at most 512); both are within the FP32 error bound, their results
+                              differ in the last bits (default 0) */
   ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook: a non-zero value makes
                                       block 0 of the next coarse-chain launch skip its first
                                       grid-barrier arrival, so every block's bounded wait

@@ -245,6 +245,10 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "CHAIN must be 0, 1 or 2");
       c->chain_mode = (int)v;
       return ARP_OK;
+    case ARP_OPT_FINE_BLOCK:
+      if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1 or 2");
+      c->fine_block = (int)v;
+      return ARP_OK;
     case ARP_OPT_TEST_SKIP_ARRIVAL:
       c->skip_arrival = (v != 0.0);
       return ARP_OK;

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <new>
 #include <string>
 #include <utility>
@@ -18,8 +19,8 @@
 
 namespace arp {
 
-arp_status launch_fine_batch_f64(arp_ctx*, int, const void*, const int*, int, int, cudaStream_t);
-arp_status launch_fine_batch_f32(arp_ctx*, int, const void*, const int*, int, int, cudaStream_t);
+arp_status launch_fine_batch_f64(arp_ctx*, arp_ctx*, int, const void*, const int*, int, int, cudaStream_t);
+arp_status launch_fine_batch_f32(arp_ctx*, arp_ctx*, int, const void*, const int*, int, int, cudaStream_t);
 arp_status plan_chain_batch_f64(int, const int*, const int*, int, int*, ClusterPlan*, size_t*);
 arp_status plan_chain_batch_f32(int, const int*, const int*, int, int*, ClusterPlan*, size_t*);
 arp_status launch_chain_batch_f64(arp_ctx*, int, const void*, int, int, size_t, cudaStream_t);
@@ -191,9 +192,10 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
     for (int i : iter) std::swap(b->ctx[i]->U, b->ctx[i]->Uold);
   };
 
-  // groups by (log2 N, precision)
-  std::map<std::pair<int, int>, std::vector<int>> groups;
-  for (int i : act) groups[{b->ctx[i]->logN, b->ctx[i]->precision}].push_back(i);
+  // groups by (log2 N, precision, ARP_OPT_FINE_BLOCK): members of a group share
+  // fused launches, so each gets the block size it would get on its own
+  std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+  for (int i : act) groups[{b->ctx[i]->logN, b->ctx[i]->precision, b->ctx[i]->fine_block}].push_back(i);
 
   int* first = reinterpret_cast<int*>(H + L.first);
   int nfirst = 0;  // ints used in the prefix region
@@ -202,14 +204,15 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
     size_t fine_off, first_fine, corr_off, first_corr, chain_off;
     int nfine, fine_blocks, ncorr, corr_blocks, nchain, C;
     size_t smem;
+    arp_ctx* tune;              // first member with a fine sweep: sets the FP32 block size
     std::vector<int> fallback;  // contexts whose chain runs on its own
   };
   std::vector<Launch> launches;
   size_t fine_bytes = 0, chain_bytes = 0, corr_count = 0;
   for (auto& g : groups) {
     Launch l{};
-    l.logN = g.first.first;
-    l.prec = g.first.second;
+    l.logN = std::get<0>(g.first);
+    l.prec = std::get<1>(g.first);
     const bool f32 = (l.prec == ARP_FP32);
     // fine sweeps and corrections of the contexts past their predictor
     l.fine_off = L.fine + fine_bytes;
@@ -218,6 +221,7 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
     for (int i : g.second) {
       arp_ctx* c = b->ctx[i];
       if (c->level < 0) continue;
+      if (!l.tune) l.tune = c;
       first[nfirst + l.nfine] = l.fine_blocks;
       if (f32) {
         FineJob<float> j{c->Uold, c->Fb, c->steps, fine_tabs<float>(c)};
@@ -296,8 +300,8 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   for (auto& l : launches) {
     const bool f32 = (l.prec == ARP_FP32);
     if (l.nfine > 0) {
-      r = f32 ? launch_fine_batch_f32(ec, l.logN, b->dmem + l.fine_off, dfirst + l.first_fine, l.nfine, l.fine_blocks, s)
-              : launch_fine_batch_f64(ec, l.logN, b->dmem + l.fine_off, dfirst + l.first_fine, l.nfine, l.fine_blocks, s);
+      r = f32 ? launch_fine_batch_f32(ec, l.tune, l.logN, b->dmem + l.fine_off, dfirst + l.first_fine, l.nfine, l.fine_blocks, s)
+              : launch_fine_batch_f64(ec, l.tune, l.logN, b->dmem + l.fine_off, dfirst + l.first_fine, l.nfine, l.fine_blocks, s);
       if (r != ARP_OK) break;
       corr_batch_kernel<<<l.corr_blocks, 256, 0, s>>>(reinterpret_cast<const CorrJob*>(b->dmem + l.corr_off),
                                                       dfirst + l.first_corr, l.ncorr);

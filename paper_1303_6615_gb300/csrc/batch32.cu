@@ -3,18 +3,18 @@
 
 namespace arp {
 
-arp_status launch_fine_batch_f32(arp_ctx* err, int logN, const void* jobs, const int* first, int njobs, int nblocks,
+arp_status launch_fine_batch_f32(arp_ctx* err, arp_ctx* tune, int logN, const void* jobs, const int* first, int njobs, int nblocks,
                                     cudaStream_t s) {
   switch (logN) {
-    case 3: return launch_fine_batch_n<float, 3>(err, jobs, first, njobs, nblocks, s);
-    case 4: return launch_fine_batch_n<float, 4>(err, jobs, first, njobs, nblocks, s);
-    case 5: return launch_fine_batch_n<float, 5>(err, jobs, first, njobs, nblocks, s);
-    case 6: return launch_fine_batch_n<float, 6>(err, jobs, first, njobs, nblocks, s);
-    case 7: return launch_fine_batch_n<float, 7>(err, jobs, first, njobs, nblocks, s);
-    case 8: return launch_fine_batch_n<float, 8>(err, jobs, first, njobs, nblocks, s);
-    case 9: return launch_fine_batch_n<float, 9>(err, jobs, first, njobs, nblocks, s);
-    case 10: return launch_fine_batch_n<float, 10>(err, jobs, first, njobs, nblocks, s);
-    case 11: return launch_fine_batch_n<float, 11>(err, jobs, first, njobs, nblocks, s);
+    case 3: return launch_fine_batch_n<float, 3>(err, tune, jobs, first, njobs, nblocks, s);
+    case 4: return launch_fine_batch_n<float, 4>(err, tune, jobs, first, njobs, nblocks, s);
+    case 5: return launch_fine_batch_n<float, 5>(err, tune, jobs, first, njobs, nblocks, s);
+    case 6: return launch_fine_batch_n<float, 6>(err, tune, jobs, first, njobs, nblocks, s);
+    case 7: return launch_fine_batch_n<float, 7>(err, tune, jobs, first, njobs, nblocks, s);
+    case 8: return launch_fine_batch_n<float, 8>(err, tune, jobs, first, njobs, nblocks, s);
+    case 9: return launch_fine_batch_n<float, 9>(err, tune, jobs, first, njobs, nblocks, s);
+    case 10: return launch_fine_batch_n<float, 10>(err, tune, jobs, first, njobs, nblocks, s);
+    case 11: return launch_fine_batch_n<float, 11>(err, tune, jobs, first, njobs, nblocks, s);
     default: return fail(err, ARP_EINVAL, "batch fine: unsupported grid size");
   }
 }

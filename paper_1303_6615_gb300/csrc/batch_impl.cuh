@@ -55,10 +55,9 @@ __global__ void __launch_bounds__(BLOCK) chain_batch_kernel(const ChainJob<T>* _
   chain_cluster_body<T, LOGN, BLOCK>(j.a, j.tb);
 }
 
-template <typename T, int LOGN>
-arp_status launch_fine_batch_n(arp_ctx* err, const void* jobs, const int* first, int njobs, int nblocks,
-                               cudaStream_t s) {
-  constexpr int BLOCK = FineBlock<LOGN>::value;
+template <typename T, int LOGN, int BLOCK>
+arp_status launch_fine_batch_block(arp_ctx* err, const void* jobs, const int* first, int njobs, int nblocks,
+                                   cudaStream_t s) {
   constexpr bool kF32 = std::is_same<T, float>::value;
   const size_t smem = kF32 ? F32Layout<LOGN, BLOCK>::kBytes : FineLayout<T, LOGN>::kBytes;
   const void* kern = (const void*)fine_batch_kernel<T, LOGN, BLOCK>;
@@ -66,6 +65,19 @@ arp_status launch_fine_batch_n(arp_ctx* err, const void* jobs, const int* first,
   if (e != cudaSuccess) return check_cuda(err, e, "batch fine: shared-memory attribute");
   void* args[] = {(void*)&jobs, (void*)&first, &njobs};
   return check_cuda(err, cudaLaunchKernel(kern, dim3(nblocks), dim3(BLOCK), args, smem, s), "batch fine: launch");
+}
+
+// `tune` is a member context of the group: its ARP_OPT_FINE_BLOCK (or the
+// per-size default) sets the FP32 block size, as for one context.
+template <typename T, int LOGN>
+arp_status launch_fine_batch_n(arp_ctx* err, arp_ctx* tune, const void* jobs, const int* first, int njobs,
+                               int nblocks, cudaStream_t s) {
+  constexpr int B0 = FineBlock<LOGN>::value, B1 = FineBlockAlt<LOGN>::value;
+  if constexpr (std::is_same<T, float>::value && B0 != B1) {
+    if (fine_choice_f32<LOGN>(tune) == 1)
+      return launch_fine_batch_block<T, LOGN, B1>(err, jobs, first, njobs, nblocks, s);
+  }
+  return launch_fine_batch_block<T, LOGN, B0>(err, jobs, first, njobs, nblocks, s);
 }
 
 // Cluster chains of `count` problems of one grid size; `plans` gets each

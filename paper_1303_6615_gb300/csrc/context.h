@@ -57,6 +57,7 @@ struct arp_ctx {
   arp::cd* V = nullptr;          // F - G
   int skip_arrival = 0;          // one-shot failure-detection test hook
   int chain_mode = 0;            // ARP_OPT_CHAIN
+  int fine_block = 0;            // ARP_OPT_FINE_BLOCK: 0 per-size default, 1 = N/4, 2 = N/2 threads
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;
 

@@ -53,6 +53,12 @@ template <int LOGN> struct FineBlock {
   static constexpr int value = N / 4 < 32 ? 32 : (N / 4 > 512 ? 512 : N / 4);
 };
 
+// Second block size of the FP32 fine sweep: N/2 threads (at most 512).
+template <int LOGN> struct FineBlockAlt {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int value = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
+};
+
 template <typename T>
 constexpr int fine_mode_arrays() {
   return std::is_same<T, float>::value ? 6 : 4;  // u, N(u), a1, acc (+ u_lo, acc_lo)
@@ -379,19 +385,48 @@ inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
           c->E_lo32, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64};
 }
 
-template <typename T, int LOGN>
-arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
-  constexpr int BLOCK = FineBlock<LOGN>::value;
+template <typename T, int LOGN, int BLOCK>
+arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int steps, cudaStream_t s) {
   constexpr bool kF32 = std::is_same<T, float>::value;
   const size_t smem = kF32 ? F32Layout<LOGN, BLOCK>::kBytes : FineLayout<T, LOGN>::kBytes;
-  const void* kern = kF32 ? (const void*)fine_sweep_kernel_f32<LOGN, BLOCK> : (const void*)fine_sweep_kernel<T, LOGN, BLOCK>;
+  const void* kern;
+  if constexpr (kF32) kern = (const void*)fine_sweep_kernel_f32<LOGN, BLOCK>;
+  else kern = (const void*)fine_sweep_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");
   FineTabs<T> tb = fine_tabs<T>(c);
-  int steps = c->steps;
   void* args[] = {(void*)&in, (void*)&out, &steps, &tb};
   e = cudaLaunchKernel(kern, dim3(batch), dim3(BLOCK), args, smem, s);
   return check_cuda(c, e, "fine: launch");
+}
+
+// Default thread count of the FP32 fine sweep per grid size: true where the
+// FineBlockAlt variant (N/2 threads) ran faster than FineBlock (N/4) on GB300
+// (256 slices of 200 to 391 steps: faster by 32% at N=128, 6% at N=256, 9% at
+// N=512, slower by 11% at N=1024; the two coincide at N<=64 and N=2048).
+// The choice is fixed per grid size, not timed at run time: the two variants
+// round differently in the last bit (the compiler contracts and schedules the
+// differently unrolled loops differently), and results must not depend on a
+// timing decision.
+template <int LOGN> struct FineAltDefault {
+  static constexpr bool value = LOGN >= 7 && LOGN <= 9;
+};
+
+// 1 when the FP32 fine sweep at this grid size runs with FineBlockAlt threads:
+// ARP_OPT_FINE_BLOCK of context c if set, else FineAltDefault.
+template <int LOGN>
+int fine_choice_f32(const arp_ctx* c) {
+  if constexpr (FineBlock<LOGN>::value == FineBlockAlt<LOGN>::value) return 0;
+  else return c->fine_block == 1 ? 0 : (c->fine_block == 2 ? 1 : (FineAltDefault<LOGN>::value ? 1 : 0));
+}
+
+template <typename T, int LOGN>
+arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
+  constexpr int B0 = FineBlock<LOGN>::value, B1 = FineBlockAlt<LOGN>::value;
+  if constexpr (std::is_same<T, float>::value && B0 != B1) {
+    if (fine_choice_f32<LOGN>(c) == 1) return launch_fine_block<T, LOGN, B1>(c, in, out, batch, c->steps, s);
+  }
+  return launch_fine_block<T, LOGN, B0>(c, in, out, batch, c->steps, s);
 }
 
 template <typename T>

@@ -131,3 +131,45 @@ def test_problem_joining_a_running_batch_and_chain_fallback():
             s.close()
     alone = _run_alone(b, probs[1], 2)
     np.testing.assert_array_equal(late, alone[1])
+
+
+
+def test_batched_members_keep_their_fine_block_size():
+    # Members of one (N, precision) group that ask for different FP32 fine-sweep
+    # block sizes (ARP_OPT_FINE_BLOCK) each get the iterates of a solo run with
+    # the same option, bit for bit.
+    torch = cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    base = PROBLEMS[3]
+    probs = [base[:8] + (40 + i,) for i in range(3)]
+    opts = [1, 2, 0]
+    alone = []
+    for p, v in zip(probs, opts):
+        with b.Solver(*p[:7], precision=p[7]) as s:
+            b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, v)
+            b.arp_set_initial(s.ctx, to_dev(_state(p[0], p[8])))
+            U = torch.empty((p[3] + 1, 3, p[0] // 2 + 1), dtype=torch.complex128, device="cuda")
+            runs = []
+            for _ in range(2):
+                b.arp_parareal_iterate(s.ctx)
+                b.arp_get_slices(s.ctx, U)
+                runs.append(to_host(U))
+            alone.append(runs)
+    solvers = [b.Solver(*p[:7], precision=p[7]) for p in probs]
+    try:
+        for s, p, v in zip(solvers, probs, opts):
+            b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, v)
+            b.arp_set_initial(s.ctx, to_dev(_state(p[0], p[8])))
+        batch = b.arp_batch_create([s.ctx for s in solvers])
+        try:
+            for k in range(2):
+                b.arp_batch_iterate(batch, len(probs))
+                for i, (s, p) in enumerate(zip(solvers, probs)):
+                    U = torch.empty((p[3] + 1, 3, p[0] // 2 + 1), dtype=torch.complex128, device="cuda")
+                    b.arp_get_slices(s.ctx, U)
+                    np.testing.assert_array_equal(to_host(U), alone[i][k])
+        finally:
+            b.arp_batch_destroy(batch)
+    finally:
+        for s in solvers:
+            s.close()

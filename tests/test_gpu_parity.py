@@ -251,6 +251,31 @@ def test_fine_fp32_small_workload_and_large_sample():
         assert per_state_rel_l2(got, ref).max() <= TOL32, w.name
 
 
+@pytest.mark.parametrize("n", [64, 128, 256, 512, 1024])
+def test_fine_fp32_block_sizes(n):
+    # The FP32 fine sweep runs with N/4 or N/2 threads per slice (ARP_OPT_FINE_BLOCK
+    # 1 or 2; 0 takes a fixed default per grid size).  Each is deterministic, both
+    # meet the FP32 bar against the oracle, and they differ only by FP32 rounding.
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    p = o.Params(n, 0.02, 1e-4 if n <= 256 else 1e-6, 0.02, 0.002, 8)
+    x = _states(n, 5, 300 + n, amp=float(n) * 2.0)
+    got = {}
+    with _solver(p, 5, precision=b.ARP_FP32) as s:
+        with pytest.raises(b.ArpError) as ei:
+            b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, 3)
+        assert ei.value.status == b.ARP_EINVAL
+        for v in (0, 1, 2):
+            b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, v)
+            got[v] = _gpu_call(b.arp_fine_batch, s, x)
+            np.testing.assert_array_equal(_gpu_call(b.arp_fine_batch, s, x), got[v])
+    assert np.array_equal(got[0], got[1]) or np.array_equal(got[0], got[2])
+    assert per_state_rel_l2(got[1], got[2]).max() <= 1e-6
+    ref = o.fine_propagate(x, p)
+    for v in (1, 2):
+        assert per_state_rel_l2(got[v], ref).max() <= TOL32, v
+
+
 def test_coarse_fp32():
     cuda_or_skip()
     from paper_1303_6615_gb300 import binding as b
