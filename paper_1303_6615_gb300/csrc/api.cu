@@ -60,7 +60,7 @@ Sizes sizes_of(int N, int slices, int M) {
   z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (size_t)N * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
              (size_t)M * 12 + K1 * 8 + 3 * K1 * 16;
   z.work = 2 * CC * 3 * K1 * 16 + (CC + 1) * P * 3 * K1 * 16 + (S + 1) * 8 + 16 + 16;
-  z.state = 2 * (S + 1) * 3 * H * 16 + 3 * S * 3 * H * 16;
+  z.state = 2 * (S + 1) * 3 * H * 16 + 3 * S * 3 * H * 16 + 2 * S * 3 * K1 * 16;
   return z;
 }
 
@@ -81,7 +81,7 @@ void release(arp_ctx* c) {
   void* ptrs[] = {c->E_lo32, c->inv_sig64, c->sk_sig64, c->inv_sig32, c->sk_sig32, c->etd64,   c->etd32, c->tw64,
                   c->tw32,      c->phase64,  c->phase32,   c->weight64,  c->weight32, c->dhalf, c->gphase,
                   c->W,         c->W2,       c->partial,   c->rel,       c->scalar,   c->U,     c->Uold,
-                  c->Gc,        c->Fb,       c->V,         c->sync,     c->part2};
+                  c->Gc,        c->Fb,       c->V,         c->sync,     c->part2,    c->VT,    c->Ge};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -118,6 +118,8 @@ arp_status allocate(arp_ctx* c) {
   ARP_ALLOC(c->Gc, S * 3 * H * 16);
   ARP_ALLOC(c->Fb, S * 3 * H * 16);
   ARP_ALLOC(c->V, S * 3 * H * 16);
+  ARP_ALLOC(c->VT, S * 3 * K1 * 16);
+  ARP_ALLOC(c->Ge, S * 3 * K1 * 16);
 #undef ARP_ALLOC
   cudaError_t e = cudaMemset(c->U, 0, (S + 1) * 3 * H * 16);
   if (e == cudaSuccess) e = cudaMemset(c->Uold, 0, (S + 1) * 3 * H * 16);

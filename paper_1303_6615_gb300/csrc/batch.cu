@@ -32,10 +32,23 @@ struct CorrJob {
   const cd* F;
   const cd* G;
   cd* V;
+  cd* VT;
   const cd* Uold0;
   cd* U0;
-  int H3;
+  int H, K1;
+  BasisTabs tb;
 };
+
+struct FinishJob {
+  const cd* Ge;
+  const cd* V;  // null: predictor
+  cd* U;
+  cd* Gc;
+  int H, K1;
+  BasisTabs tb;
+};
+
+BasisTabs basis_tabs(const arp_ctx* c) { return BasisTabs{c->inv_sig64, c->sk_sig64, c->dhalf}; }
 
 struct NormJob {
   const cd* U;
@@ -44,16 +57,21 @@ struct NormJob {
   int H, S;
 };
 
-// Blocks per (problem, slice n < S): V_n = F_n - G_n; slice 0 also copies u0 into the new iterate.
+// Blocks per (problem, slice n < S): corr_body; slice 0 also copies u0 into the new iterate.
 __global__ void corr_batch_kernel(const CorrJob* __restrict__ jobs, const int* __restrict__ first, int njobs) {
   const int i = find_job(first, njobs, blockIdx.x);
   const CorrJob j = jobs[i];
   const int n = blockIdx.x - first[i];
-  const size_t o = (size_t)n * j.H3;
-  for (int t = threadIdx.x; t < j.H3; t += blockDim.x) {
-    j.V[o + t] = j.F[o + t] - j.G[o + t];
-    if (n == 0) j.U0[t] = j.Uold0[t];
-  }
+  corr_body(j.F, j.G, j.V, j.VT, n, j.H, j.K1, j.tb);
+  if (n == 0)
+    for (int t = threadIdx.x; t < 3 * j.H; t += blockDim.x) j.U0[t] = j.Uold0[t];
+}
+
+// Blocks per (problem, slice n < S) of the problems whose chain ran in a cluster: finish_body.
+__global__ void finish_batch_kernel(const FinishJob* __restrict__ jobs, const int* __restrict__ first, int njobs) {
+  const int i = find_job(first, njobs, blockIdx.x);
+  const FinishJob j = jobs[i];
+  finish_body(j.Ge, j.V, j.U, j.Gc, blockIdx.x - first[i], j.H, j.K1, j.tb);
 }
 
 // 256-thread blocks per (problem, slice n = 1..S): the relative change of the slice.
@@ -93,7 +111,7 @@ struct arp_batch {
 namespace {
 
 struct Layout {
-  size_t fine, chain, corr, norm, first, out, total;
+  size_t fine, chain, corr, fin, norm, first, out, total;
 };
 
 Layout layout_for(int n) {
@@ -105,6 +123,8 @@ Layout layout_for(int n) {
   off += align256((size_t)n * std::max(sizeof(ChainJob<double>), sizeof(ChainJob<float>)));
   L.corr = off;
   off += align256((size_t)n * sizeof(CorrJob));
+  L.fin = off;
+  off += align256((size_t)n * sizeof(FinishJob));
   L.norm = off;
   off += align256((size_t)n * sizeof(NormJob));
   L.first = off;
@@ -201,14 +221,14 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   int nfirst = 0;  // ints used in the prefix region
   struct Launch {
     int logN, prec;
-    size_t fine_off, first_fine, corr_off, first_corr, chain_off;
-    int nfine, fine_blocks, ncorr, corr_blocks, nchain, C;
+    size_t fine_off, first_fine, corr_off, first_corr, chain_off, fin_off, first_fin;
+    int nfine, fine_blocks, ncorr, corr_blocks, nchain, C, fin_blocks;
     size_t smem;
     arp_ctx* tune;              // first member with a fine sweep: sets the FP32 block size
     std::vector<int> fallback;  // contexts whose chain runs on its own
   };
   std::vector<Launch> launches;
-  size_t fine_bytes = 0, chain_bytes = 0, corr_count = 0;
+  size_t fine_bytes = 0, chain_bytes = 0, corr_count = 0, fin_count = 0;
   for (auto& g : groups) {
     Launch l{};
     l.logN = std::get<0>(g.first);
@@ -230,7 +250,7 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
         FineJob<double> j{c->Uold, c->Fb, c->steps, fine_tabs<double>(c)};
         memcpy(H + l.fine_off + (size_t)l.nfine * sizeof(j), &j, sizeof(j));
       }
-      CorrJob cj{c->Fb, c->Gc, c->V, c->Uold, c->U, 3 * c->H};
+      CorrJob cj{c->Fb, c->Gc, c->V, c->VT, c->Uold, c->U, c->H, c->K1, basis_tabs(c)};
       memcpy(H + l.corr_off + (size_t)l.ncorr * sizeof(CorrJob), &cj, sizeof(cj));
       l.fine_blocks += c->slices;
       ++l.nfine;
@@ -256,12 +276,18 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
       pr = f32 ? plan_chain_batch_f32(l.logN, M.data(), K1.data(), (int)M.size(), &l.C, plans.data(), &l.smem)
                : plan_chain_batch_f64(l.logN, M.data(), K1.data(), (int)M.size(), &l.C, plans.data(), &l.smem);
     l.chain_off = L.chain + chain_bytes;
+    l.fin_off = L.fin + fin_count * sizeof(FinishJob);
+    l.first_fin = nfirst;
     if (pr == ARP_OK) {
       for (size_t t = 0; t < g.second.size(); ++t) {
         arp_ctx* c = b->ctx[g.second[t]];
         const ClusterPlan& p = plans[t];
-        ClusterChainArgs a{c->level >= 0 ? c->V : nullptr, c->U, c->Gc, c->slices, c->M, p.q, p.own, p.ph_smem,
+        ClusterChainArgs a{c->level >= 0 ? c->VT : nullptr, c->U, c->Ge, c->slices, c->M, p.q, p.own, p.ph_smem,
                            p.tmp_smem, c->dT, c->inv_sig64, c->sk_sig64, c->dhalf, c->gphase};
+        FinishJob fj{c->Ge, c->level >= 0 ? c->V : nullptr, c->U, c->Gc, c->H, c->K1, basis_tabs(c)};
+        memcpy(H + l.fin_off + t * sizeof(FinishJob), &fj, sizeof(fj));
+        first[nfirst + t] = l.fin_blocks;
+        l.fin_blocks += c->slices;
         if (f32) {
           ChainJob<float> j{a, nbar_tabs<float>(c)};
           memcpy(H + l.chain_off + t * sizeof(j), &j, sizeof(j));
@@ -271,6 +297,9 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
         }
       }
       l.nchain = (int)g.second.size();
+      first[nfirst + l.nchain] = l.fin_blocks;
+      nfirst += l.nchain + 1;
+      fin_count += l.nchain;
       chain_bytes += (size_t)l.nchain * (f32 ? sizeof(ChainJob<float>) : sizeof(ChainJob<double>));
     } else {
       l.fallback = g.second;
@@ -311,6 +340,9 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
       r = f32 ? launch_chain_batch_f32(ec, l.logN, b->dmem + l.chain_off, l.nchain, l.C, l.smem, s)
               : launch_chain_batch_f64(ec, l.logN, b->dmem + l.chain_off, l.nchain, l.C, l.smem, s);
       if (r != ARP_OK) break;
+      finish_batch_kernel<<<l.fin_blocks, 256, 0, s>>>(reinterpret_cast<const FinishJob*>(b->dmem + l.fin_off),
+                                                       dfirst + l.first_fin, l.nchain);
+      if ((r = check_cuda(ec, cudaGetLastError(), "batch: finish")) != ARP_OK) break;
     }
     for (int i : l.fallback) {
       arp_ctx* c = b->ctx[i];

@@ -9,14 +9,27 @@
 // weighted, back-rotated terms in node order.  The sum over CTAs, and the
 // exchange of the next state, are stores into other CTAs' shared memory
 // (distributed shared memory) between hardware cluster barriers -- no
-// global-memory atomics, no spin-waits:
+// global-memory atomics, no spin-waits.  Per time average:
 //   1  every CTA: its nodes' partial sum for the current state WS, stored
 //      into the reduction buffer RED[rank] of each wavenumber's owner CTA
 //   2  cluster barrier
-//   3  CTA j, for its own wavenumbers: the sum of RED over the C ranks (fixed
-//      order), then the FP64 epilogue (midpoint state, or g, U_{n+1}, G cache
-//      and the next w); the result's float copy is stored into WS of every CTA
+//   3  CTA j, for its own (branch, wavenumber) pairs, one thread each: the sum
+//      of RED over the C ranks (fixed order), the FP64 epilogue (the midpoint
+//      state, or g and the next w), and the float copy of the result stored
+//      into WS of every CTA
 //   4  cluster barrier
+// Only what the next link needs stays on this serial path, and GB300's FP64
+// units (1/64 of the FP32 rate) make every FP64 instruction on it costly:
+//   - the chain writes g_n = G(U_n) in the eigen basis (Ge) and leaves the
+//     basis change U_{n+1} = R g_n + V_n, the G cache R g_n and the
+//     truncated modes to a parallel kernel afterwards (finish_body);
+//   - the next w needs no basis change either: R is unitary, so
+//     e^{dT/2 D} R^H (R g + V_n) = e^{dT/2 D} g + VT_n, with
+//     VT_n = e^{dT/2 D} R^H V_n formed for all links in parallel beforehand
+//     (corr_body) and prefetched two links ahead.  (Before that basis change
+//     the oracle also drops the rounding-level imaginary part of R g at
+//     k = 0; here that projection reaches U and the G cache, not w: a
+//     difference at the rounding level.)
 // The FP64 state w of a wavenumber lives only in its owner CTA, so every
 // exchanged copy is freshly rounded from FP64.
 #pragma once
@@ -28,9 +41,9 @@
 namespace arp {
 
 struct ClusterChainArgs {
-  const cd* V;       // [S][3][H] or null (predictor)
-  cd* U;             // [(S+1)][3][H]; U_0 read, U_1..U_S written
-  cd* Gc;            // [S][3][H] written
+  const cd* VT;      // [S][3][K1] e^{dT/2 D} R^H V_n (eigen basis), or null (predictor: V = 0)
+  const cd* U0;      // [3][H] the chain's initial state U_0
+  cd* Ge;            // [S][3][K1] g_n = G(U_n) in the eigen basis, written
   int S, M, q, own;  // links, nodes, nodes per CTA, wavenumbers per CTA
   int ph_smem;       // node phases staged in shared memory (else read from the table)
   int tmp_smem;      // per-node terms staged for a balanced node sum (else summed per wavenumber)
@@ -45,13 +58,13 @@ template <int LOGN> struct ClusterBlock {
   static constexpr int value = (1 << LOGN) <= 256 ? 256 : 512;
 };
 
-// Shared memory: FP64 per own wavenumber (w, gphase for 3 branches, V of the
-// link for 3 fields, dhalf, the two eigen constants), the FFT lanes, twiddles,
+// Shared memory: FP64 per own wavenumber (w and e^{dT/2 D} gphase for 3
+// branches, dhalf, the two eigen constants), the FFT lanes, twiddles,
 // the node phases [q][3][K1] and weights, WS/ACC/EXCH and the eigen constants.
 template <typename T>
 inline size_t cluster_chain_smem_bytes(int logn, int q, int own, int C, bool ph_smem, bool tmp_smem) {
   const int K1 = ((1 << logn) - 1) / 3 + 1;
-  return (size_t)12 * own * sizeof(cd) + (size_t)3 * own * sizeof(double) +
+  return (size_t)6 * own * sizeof(cd) + (size_t)3 * own * sizeof(double) +
          (size_t)(2 * q * padded_len<T>(1 << logn) + twiddle_count(logn) + (ph_smem ? 3 * q * K1 : 0) + 3 * K1 +
                   (tmp_smem ? 3 * q * K1 : 0) + 3 * C * own) *
              sizeof(cpx<T>) +
@@ -78,10 +91,8 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
   // (16-byte elements), then complex T arrays, then FP64 scalars, then T scalars.
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cd* W64 = reinterpret_cast<cd*>(smem_raw);  // [3][own] FP64 w of the own wavenumbers
-  cd* GPH = W64 + 3 * own;                    // [3][own] e^{-i omega dT/eps}
-  cd* VL = GPH + 3 * own;                     // [3][own] V_n of the link (fields)
-  cd* EP = VL + 3 * own;                      // [3][own] epilogue temporaries
-  cpx<T>* Z = reinterpret_cast<cpx<T>*>(EP + 3 * own);
+  cd* GPH = W64 + 3 * own;                    // [3][own] e^{dT/2 D} e^{-i omega dT/eps}
+  cpx<T>* Z = reinterpret_cast<cpx<T>*>(GPH + 3 * own);
   cpx<T>* TW = Z + 2 * q * PL;
   cpx<T>* PHs = TW + twiddle_count(LOGN);     // [q][3][K1] phases of this CTA's nodes
   cpx<T>* WS = PHs + (a.ph_smem ? 3 * q * K1 : 0);  // [3][K1] state, written by the owners
@@ -108,35 +119,41 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
     IS64[k - k0] = a.is64[k];
     SS64[k - k0] = a.ss64[k];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) GPH[b * own + (k - k0)] = a.gphase[b * K1 + k];
+    for (int b = 0; b < 3; ++b) GPH[b * own + (k - k0)] = a.dhalf[k] * a.gphase[b * K1 + k];
   }
   // w = e^{dT/2 D} R^H U_0 for the own wavenumbers; its float copy into every CTA's WS
   for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
     cd x[3], e[3];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      x[f] = a.U[f * H + k];
+      x[f] = a.U0[f * H + k];
       if (k == 0) x[f].y = 0.0;
     }
     phys_to_eigen<double>(x, a.is64[k], a.ss64[k], e);
 #pragma unroll
     for (int b = 0; b < 3; ++b) W64[b * own + (k - k0)] = a.dhalf[k] * e[b];
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < C * 3 * (k1 - k0); t += BLOCK) {
-    const int c = t / (3 * (k1 - k0)), r3 = t - c * 3 * (k1 - k0);
-    const int b = r3 / (k1 - k0), r = r3 - b * (k1 - k0);
+  // owner thread t < 3 no: branch b and own wavenumber r; it keeps VT of the
+  // next two links for its pair in registers
+  const int no = k1 - k0;
+  const bool owner_t = (int)threadIdx.x < 3 * no;
+  const int ob = owner_t ? (int)threadIdx.x / no : 0;
+  const int orr = owner_t ? (int)threadIdx.x - ob * no : 0;
+  const int ok = k0 + orr;
+  auto load_vt = [&](int n) {
+    return (a.VT && owner_t && n < a.S) ? a.VT[((size_t)n * 3 + ob) * K1 + ok] : cd{0.0, 0.0};
+  };
+  cd vt_cur = load_vt(0), vt_nxt = load_vt(1);
+  __syncthreads();  // W64
+  for (int t = threadIdx.x; t < C * 3 * no; t += BLOCK) {
+    const int c = t / (3 * no), r3 = t - c * 3 * no;
+    const int b = r3 / no, r = r3 - b * no;
     cl.map_shared_rank(WS, c)[b * K1 + k0 + r] = cvt<T>(W64[b * own + r]);
   }
   cl.sync();
 
 #pragma unroll 1
   for (int n = 0; n < a.S; ++n) {
-    // V_n of the own wavenumbers, fetched now so its latency hides behind the evaluations
-    for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
-#pragma unroll
-      for (int f = 0; f < 3; ++f) VL[f * own + (k - k0)] = a.V ? a.V[((size_t)n * 3 + f) * H + k] : cd{0.0, 0.0};
-    }
 #pragma unroll 1
     for (int round = 0; round < 2; ++round) {
       // 1: this CTA's nodes, all at once
@@ -189,59 +206,26 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
         }
       }
       cl.sync();  // 2
-      // 3: own wavenumbers: sum over the ranks in rank order, FP64 epilogue
-      const int no = k1 - k0;
-      for (int t = threadIdx.x; t < 3 * no; t += BLOCK) {
-        const int b = t / no, r = t - b * no;
-        cpx<T> s = mk<T>(0, 0);
-        for (int c = 0; c < C; ++c) s = s + RED[(c * 3 + b) * own + r];
-        const cd sum = cvt<double>(s);
-        if (round == 0)  // midpoint state w + dT/2 k1
-          EP[b * own + r] = W64[b * own + r] + (0.5 * a.dT) * sum;
-        else  // g = e^{-(dT/eps) L} e^{dT/2 D} (w + dT k2), per branch
-          EP[b * own + r] = DH[r] * (GPH[b * own + r] * (W64[b * own + r] + a.dT * sum));
-      }
-      __syncthreads();
-      const bool last = (round == 1 && n == a.S - 1);
-      if (round == 1) {
-        // U_{n+1} = R g + V_n and the G cache, per wavenumber; next w = e^{dT/2 D} R^H U_{n+1}
-        cd* gout = a.Gc + (size_t)n * 3 * H;
-        cd* uout = a.U + (size_t)(n + 1) * 3 * H;
-        for (int r = threadIdx.x; r < no; r += BLOCK) {
-          const int k = k0 + r;
-          cd g[3], u[3], e[3];
-#pragma unroll
-          for (int b = 0; b < 3; ++b) g[b] = EP[b * own + r];
-          eigen_to_phys<double>(g, IS64[r], SS64[r], u);
-#pragma unroll
-          for (int f = 0; f < 3; ++f) {
-            if (k == 0) u[f].y = 0.0;
-            gout[f * H + k] = u[f];
-            u[f] = u[f] + VL[f * own + r];
-            uout[f * H + k] = u[f];
-          }
-          phys_to_eigen<double>(u, IS64[r], SS64[r], e);
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            W64[b * own + r] = DH[r] * e[b];
-            EP[b * own + r] = W64[b * own + r];
-          }
+      // 3: own (branch, wavenumber): sum over the ranks in rank order, FP64
+      // epilogue, and the float copy of the result into every CTA's WS
+      if (owner_t) {
+        cpx<T> sr = mk<T>(0, 0);
+        for (int c = 0; c < C; ++c) sr = sr + RED[(c * 3 + ob) * own + orr];
+        const cd sum = cvt<double>(sr);
+        const int i = ob * own + orr;
+        cd v;
+        if (round == 0) {  // midpoint state w + dT/2 k1
+          v = W64[i] + (0.5 * a.dT) * sum;
+        } else {  // g = e^{dT/2 D} e^{-(dT/eps) L} (w + dT k2); next w = e^{dT/2 D} g + VT_n
+          const cd g = GPH[i] * (W64[i] + a.dT * sum);
+          a.Ge[((size_t)n * 3 + ob) * K1 + ok] = g;
+          v = DH[orr] * g + vt_cur;
+          W64[i] = v;
+          vt_cur = vt_nxt;
+          vt_nxt = load_vt(n + 2);
         }
-        if (j == 0) {
-          for (int t = threadIdx.x; t < 3 * (H - K1); t += BLOCK) {
-            const int f = t / (H - K1), k = K1 + t % (H - K1);
-            gout[f * H + k] = {0.0, 0.0};
-            uout[f * H + k] = {0.0, 0.0};
-          }
-        }
-        __syncthreads();
-      }
-      if (last) break;
-      // 4: the float copy of the new own values into every CTA's WS
-      for (int t = threadIdx.x; t < C * 3 * no; t += BLOCK) {
-        const int c = t / (3 * no), r3 = t - c * 3 * no;
-        const int b = r3 / no, r = r3 - b * no;
-        cl.map_shared_rank(WS, c)[b * K1 + k0 + r] = cvt<T>(EP[b * own + r]);
+        const cpx<T> vt = cvt<T>(v);
+        for (int c = 0; c < C; ++c) cl.map_shared_rank(WS, c)[ob * K1 + ok] = vt;
       }
       cl.sync();  // 4
     }
@@ -308,10 +292,11 @@ inline bool cluster_config(const void* kern, int C, int block, size_t smem, int 
   return true;
 }
 
-// Launches the cluster chain; ARP_EINVAL (nothing launched) if no cluster of 16
-// or 8 CTAs with this kernel's shared memory can be scheduled.
+// Launches the cluster chain (g_n into Ge; U and the G cache follow from
+// finish_body); ARP_EINVAL (nothing launched) if no cluster of 16 or 8 CTAs
+// with this kernel's shared memory can be scheduled.
 template <typename T, int LOGN>
-arp_status launch_cluster_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
+arp_status launch_cluster_chain_n(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s) {
   constexpr int BLOCK = ClusterBlock<LOGN>::value;
   const void* kern = (const void*)chain_cluster_kernel<T, LOGN, BLOCK>;
   for (int C : {16, 8}) {
@@ -319,7 +304,7 @@ arp_status launch_cluster_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaSt
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     if (!cluster_config(kern, C, BLOCK, p.smem, 1, s, &cfg, attr)) continue;
-    ClusterChainArgs a{V, U, Gc, c->slices, c->M, p.q, p.own, p.ph_smem, p.tmp_smem, c->dT, c->inv_sig64,
+    ClusterChainArgs a{VT, U0, Ge, c->slices, c->M, p.q, p.own, p.ph_smem, p.tmp_smem, c->dT, c->inv_sig64,
                        c->sk_sig64, c->dhalf, c->gphase};
     NbarTabs<T> tb = nbar_tabs<T>(c);
     void* args[] = {&a, &tb};
@@ -329,17 +314,17 @@ arp_status launch_cluster_chain_n(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaSt
 }
 
 template <typename T>
-arp_status launch_cluster_chain_prec(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {
+arp_status launch_cluster_chain_prec(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s) {
   switch (c->logN) {
-    case 3: return launch_cluster_chain_n<T, 3>(c, U, Gc, V, s);
-    case 4: return launch_cluster_chain_n<T, 4>(c, U, Gc, V, s);
-    case 5: return launch_cluster_chain_n<T, 5>(c, U, Gc, V, s);
-    case 6: return launch_cluster_chain_n<T, 6>(c, U, Gc, V, s);
-    case 7: return launch_cluster_chain_n<T, 7>(c, U, Gc, V, s);
-    case 8: return launch_cluster_chain_n<T, 8>(c, U, Gc, V, s);
-    case 9: return launch_cluster_chain_n<T, 9>(c, U, Gc, V, s);
-    case 10: return launch_cluster_chain_n<T, 10>(c, U, Gc, V, s);
-    case 11: return launch_cluster_chain_n<T, 11>(c, U, Gc, V, s);
+    case 3: return launch_cluster_chain_n<T, 3>(c, U0, Ge, VT, s);
+    case 4: return launch_cluster_chain_n<T, 4>(c, U0, Ge, VT, s);
+    case 5: return launch_cluster_chain_n<T, 5>(c, U0, Ge, VT, s);
+    case 6: return launch_cluster_chain_n<T, 6>(c, U0, Ge, VT, s);
+    case 7: return launch_cluster_chain_n<T, 7>(c, U0, Ge, VT, s);
+    case 8: return launch_cluster_chain_n<T, 8>(c, U0, Ge, VT, s);
+    case 9: return launch_cluster_chain_n<T, 9>(c, U0, Ge, VT, s);
+    case 10: return launch_cluster_chain_n<T, 10>(c, U0, Ge, VT, s);
+    case 11: return launch_cluster_chain_n<T, 11>(c, U0, Ge, VT, s);
     default: return fail(c, ARP_EINVAL, "cluster chain: unsupported grid size");
   }
 }

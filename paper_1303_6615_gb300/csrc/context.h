@@ -55,6 +55,8 @@ struct arp_ctx {
   arp::cd* Gc = nullptr;         // G(U_n) of the current iterate, n < slices
   arp::cd* Fb = nullptr;         // F(U_n), n < slices
   arp::cd* V = nullptr;          // F - G
+  arp::cd* VT = nullptr;         // [slices][3][K1] e^{dT/2 D} R^H V_n (eigen basis)
+  arp::cd* Ge = nullptr;         // [slices][3][K1] G(U_n) in the eigen basis (cluster chain)
   int skip_arrival = 0;          // one-shot failure-detection test hook
   int chain_mode = 0;            // ARP_OPT_CHAIN
   int fine_block = 0;            // ARP_OPT_FINE_BLOCK: 0 per-size default, 1 = N/4, 2 = N/2 threads
@@ -99,7 +101,7 @@ arp_status coarse_step(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_
 arp_status launch_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
 // The same chain inside one thread-block cluster (no grid barriers).  Returns
 // ARP_EINVAL (without launching) if no suitable cluster can be scheduled.
-arp_status launch_cluster_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
+arp_status launch_cluster_chain(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s);
 
 // parareal.cu
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);

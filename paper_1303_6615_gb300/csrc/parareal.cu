@@ -14,9 +14,14 @@
 
 namespace arp {
 
-__global__ void correction_kernel(const cd* __restrict__ f, const cd* __restrict__ g, cd* __restrict__ v, size_t n) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = f[i] - g[i];
+__global__ void correction_kernel(const cd* __restrict__ F, const cd* __restrict__ G, cd* __restrict__ V,
+                                  cd* __restrict__ VT, int H, int K1, BasisTabs tb) {
+  corr_body(F, G, V, VT, blockIdx.x, H, K1, tb);
+}
+
+__global__ void finish_kernel(const cd* __restrict__ Ge, const cd* __restrict__ V, cd* __restrict__ U,
+                              cd* __restrict__ Gc, int H, int K1, BasisTabs tb) {
+  finish_body(Ge, V, U, Gc, blockIdx.x, H, K1, tb);
 }
 
 __global__ void slice_change_kernel(const cd* __restrict__ U, const cd* __restrict__ Uold, double* __restrict__ rel,
@@ -32,6 +37,8 @@ __global__ void max_kernel(const double* __restrict__ rel, int S, double* __rest
 }
 
 namespace {
+
+BasisTabs basis_tabs(const arp_ctx* c) { return BasisTabs{c->inv_sig64, c->sk_sig64, c->dhalf}; }
 
 // G(U_n) for the single state at U + n, written to g_out; u_next = g (+ v), with
 // one launch per step of the link (used when the persistent chain cannot be
@@ -54,17 +61,25 @@ arp_status chain_status(arp_ctx* c, unsigned status) {
 
 }  // namespace
 
-// The whole serial chain n = 0..S-1: one thread-block cluster, else the
+// The whole serial chain n = 0..S-1: one thread-block cluster (then the
+// parallel finish: U and the G cache from the eigen-basis g_n), else the
 // persistent cooperative kernel, else one link at a time (ARP_OPT_CHAIN
 // restricts the choice; the barrier-timeout test hook needs the cooperative
-// kernel, whose grid barriers are the bounded waits it exercises).
+// kernel, whose grid barriers are the bounded waits it exercises).  V, if not
+// null, is c->V, whose eigen form c->VT the correction kernel wrote with it.
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   const size_t st = (size_t)3 * c->H;
   // barrier counter and status word start at zero whichever kernel runs
   arp_status r = check_cuda(c, cudaMemsetAsync(c->sync, 0, 4 * sizeof(unsigned), s), "chain: status reset");
   if (r != ARP_OK) return r;
   r = ARP_EINVAL;
-  if (c->chain_mode == 0 && !c->skip_arrival) r = launch_cluster_chain(c, c->U, c->Gc, V, s);
+  if (c->chain_mode == 0 && !c->skip_arrival) {
+    r = launch_cluster_chain(c, c->U, c->Ge, V ? c->VT : nullptr, s);
+    if (r == ARP_OK) {
+      finish_kernel<<<c->slices, 256, 0, s>>>(c->Ge, V, c->U, c->Gc, c->H, c->K1, basis_tabs(c));
+      r = check_cuda(c, cudaGetLastError(), "chain: finish");
+    }
+  }
   if (r != ARP_EINVAL) return r;
   if (c->chain_mode <= 1) r = launch_chain(c, c->U, c->Gc, V, s);
   if (r != ARP_EINVAL) return r;
@@ -95,8 +110,7 @@ arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* cha
   }
   std::swap(c->U, c->Uold);
   if ((r = launch_fine(c, c->Uold, c->Fb, S, s)) != ARP_OK) return r;
-  const size_t nv = (size_t)S * st;
-  correction_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(c->Fb, c->Gc, c->V, nv);
+  correction_kernel<<<S, 256, 0, s>>>(c->Fb, c->Gc, c->V, c->VT, c->H, c->K1, basis_tabs(c));
   if ((r = check_cuda(c, cudaGetLastError(), "correction: launch")) != ARP_OK) return r;
   if ((r = check_cuda(c, cudaMemcpyAsync(c->U, c->Uold, st * sizeof(cd), cudaMemcpyDeviceToDevice, s),
                       "copy u0")) != ARP_OK)
