@@ -34,6 +34,9 @@ Functions and the passages they follow:
   rho, quadrature      kernel and nodes of Eq. 2.1-2.2 and Algorithm 1
   nbar                 finite, discretised average of Eq. 2.1 (Algorithm 1)
   coarse_step          asymptotic slow solver (Algorithm 2)
+  strang_step/strang_propagate   Strang-splitting fine solver (Algorithm 3)
+  coarse_step_strang   one Strang step over dT: the coarse solver of standard
+                       parareal on the full equation (Sec. 6.2)
   parareal             the iteration of Eq. 3.1 (Algorithm 4)
   rel_change_norm      stopping quantity of Algorithm 4
   estimated_speedup    complexity model of Eq. 5.1
@@ -305,6 +308,51 @@ def fine_propagate(u: np.ndarray, p: Params, nl: NonlinearFn = nonlinear,
     for _ in range(steps):
         u = fine_step(u, p, h, nl)
     return u
+
+
+# ---------------------------------------------------------------------------
+# Strang splitting (Algorithm 3) and standard parareal's coarse solver (Sec. 6.2)
+# ---------------------------------------------------------------------------
+
+def _linear_half(p: Params, h: float) -> np.ndarray:
+    key = ("lin_half", h, p.eps, p.nu, p.n_grid, p.F)
+    if key not in p._cache:
+        p._cache[key] = linear_matrices(p, h / 2.0)
+    return p._cache[key]
+
+
+def strang_step(u: np.ndarray, p: Params, h: float, nl: NonlinearFn = nonlinear) -> np.ndarray:
+    """One Strang-splitting step of size h (Algorithm 3): an exact half step of
+    the linear part, a midpoint step of the nonlinear part, an exact half step.
+    The nonlinear stage is read as in Algorithm 2:
+        w = e^{h/2 (-L/eps + D)} u;  k1 = N(w);  k2 = N(w + h/2 k1);  w = w + h k2;
+        return e^{h/2 (-L/eps + D)} w."""
+    E2 = _linear_half(p, h)
+    n = p.n_grid
+    w = _apply(E2, u)
+    k1 = nl(w, n)
+    k2 = nl(w + (h / 2.0) * k1, n)
+    w = w + h * k2
+    return _apply(E2, w)
+
+
+def strang_propagate(u: np.ndarray, p: Params, nl: NonlinearFn = nonlinear,
+                     steps: Optional[int] = None) -> np.ndarray:
+    """The Strang-splitting fine propagator over one coarse interval dT."""
+    if steps is None:
+        steps, h = fine_steps(p.dT, p.dt)
+    else:
+        h = p.dT / steps
+    u = project(u, p.n_grid)
+    for _ in range(steps):
+        u = strang_step(u, p, h, nl)
+    return u
+
+
+def coarse_step_strang(u: np.ndarray, p: Params, nl: NonlinearFn = nonlinear) -> np.ndarray:
+    """Standard parareal's coarse solver (Sec. 6.2): one Strang step of size dT
+    of the full equation."""
+    return strang_step(project(u, p.n_grid), p, p.dT, nl)
 
 
 # ---------------------------------------------------------------------------

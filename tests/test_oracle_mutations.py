@@ -8,6 +8,7 @@ import test_oracle_coarse as tc
 import test_oracle_fine as tf
 import test_oracle_model as tm
 import test_oracle_parareal as tp
+import test_oracle_strang as ts
 
 
 def _bad_nl_sign(u, n):
@@ -48,8 +49,24 @@ def _bad_quadrature(p):
     return s + p.window / p.m_quad / 2, w        # nodes shifted by half a spacing
 
 
+def _bad_strang_one_half_step(u, p, h, nl=None):
+    nl = nl or rsw.nonlinear
+    w = rsw._apply(rsw.linear_matrices(p, h / 2.0), u)   # second linear half step dropped
+    k1 = nl(w, p.n_grid)
+    return w + h * nl(w + h / 2 * k1, p.n_grid)
+
+
+def _bad_strang_stage_from_u(u, p, h, nl=None):
+    nl = nl or rsw.nonlinear
+    E2 = rsw.linear_matrices(p, h / 2.0)
+    w = rsw._apply(E2, u)
+    k1 = nl(w, p.n_grid)
+    k2 = nl(u + h / 2 * k1, p.n_grid)                    # midpoint stage built on u, not w
+    return rsw._apply(E2, w + h * k2)
+
+
 _orig = {name: getattr(rsw, name) for name in
-         ("nonlinear", "phi123", "etdrk4_coefficients", "expL", "_apply", "quadrature")}
+         ("nonlinear", "phi123", "etdrk4_coefficients", "expL", "_apply", "quadrature", "strang_step")}
 
 CASES = [
     ("nonlinear", _bad_nl_sign, tm.test_nonlinearity_analytic_case, ()),
@@ -60,6 +77,8 @@ CASES = [
     ("expL", _bad_expL, tc.test_coarse_step_linear_part_exact, ()),
     ("_apply", _bad_apply, tf.test_linear_part_is_exact, ()),
     ("quadrature", _bad_quadrature, tc.test_quadrature_weights_sum_to_one, (32,)),
+    ("strang_step", _bad_strang_one_half_step, ts.test_strang_linear_part_is_exact, ()),
+    ("strang_step", _bad_strang_stage_from_u, ts.test_strang_second_order_convergence, ()),
 ]
 
 
