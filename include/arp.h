@@ -74,6 +74,16 @@ typedef enum {
                               size (the faster on GB300), 1 = N/4, 2 = N/2 (both at least 32,
                               at most 512); both are within the FP32 error bound, their results
                               differ in the last bits (default 0) */
+  ARP_OPT_FINE_SCHEME = 8,  /* fine propagator F: 0 = ETDRK4 (Cox & Matthews, default), 1 = Strang
+                               splitting (Algorithm 3: exact linear half steps around a midpoint
+                               step of N, steps of size h = dT/ceil(dT/dt)); used by
+                               arp_fine_batch and the parareal iteration */
+  ARP_OPT_COARSE_SCHEME = 9,  /* coarse propagator G: 0 = the asymptotic slow solver
+                                 (Algorithm 2, default), 1 = one Strang step of size dT of the
+                                 full equation (standard parareal, Sec. 6.2); used by
+                                 arp_coarse_step and the parareal chain.  arp_coarse_avg always
+                                 computes the time average.  Batches (arp_batch_*) accept only
+                                 the default schemes (ARP_EINVAL otherwise) */
   ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook: a non-zero value makes
                                       block 0 of the next coarse-chain launch skip its first
                                       grid-barrier arrival, so every block's bounded wait

@@ -21,6 +21,8 @@ ARP_FP64, ARP_FP32 = 0, 1
 ARP_OPT_T0, ARP_OPT_F, ARP_OPT_PRECISION, ARP_OPT_KMAX, ARP_OPT_TOL = 1, 2, 3, 4, 5
 ARP_OPT_CHAIN = 6
 ARP_OPT_FINE_BLOCK = 7
+ARP_OPT_FINE_SCHEME = 8
+ARP_OPT_COARSE_SCHEME = 9
 ARP_OPT_TEST_SKIP_ARRIVAL = 100
 STATUS_NAMES = {0: "ARP_OK", 1: "ARP_EINVAL", 2: "ARP_ENOMEM", 3: "ARP_ECUDA", 4: "ARP_ETIMEOUT",
                 5: "ARP_ENONFINITE"}

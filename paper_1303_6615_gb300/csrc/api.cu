@@ -58,7 +58,7 @@ Sizes sizes_of(int N, int slices, int M) {
   const size_t CC = coarse_chunk(slices, P, K1);
   Sizes z;
   z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (size_t)N * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
-             (size_t)M * 12 + K1 * 8 + 3 * K1 * 16;
+             (size_t)M * 12 + K1 * 8 + 3 * K1 * 16 + 3 * K1 * 16;
   z.work = 2 * CC * 3 * K1 * 16 + (CC + 1) * P * 3 * K1 * 16 + (S + 1) * 8 + 16 + 16;
   z.state = 2 * (S + 1) * 3 * H * 16 + 3 * S * 3 * H * 16 + 2 * S * 3 * K1 * 16;
   return z;
@@ -81,7 +81,8 @@ void release(arp_ctx* c) {
   void* ptrs[] = {c->E_lo32, c->inv_sig64, c->sk_sig64, c->inv_sig32, c->sk_sig32, c->etd64,   c->etd32, c->tw64,
                   c->tw32,      c->phase64,  c->phase32,   c->weight64,  c->weight32, c->dhalf, c->gphase,
                   c->W,         c->W2,       c->partial,   c->rel,       c->scalar,   c->U,     c->Uold,
-                  c->Gc,        c->Fb,       c->V,         c->sync,     c->part2,    c->VT,    c->Ge};
+                  c->Gc,        c->Fb,       c->V,         c->sync,     c->part2,    c->VT,    c->Ge,
+                  c->strang_h64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -106,6 +107,7 @@ arp_status allocate(arp_ctx* c) {
   ARP_ALLOC(c->weight32, M * 4);
   ARP_ALLOC(c->dhalf, K1 * 8);
   ARP_ALLOC(c->gphase, 3 * K1 * 16);
+  ARP_ALLOC(c->strang_h64, 3 * K1 * 16);
   ARP_ALLOC(c->W, CC * 3 * K1 * 16);
   ARP_ALLOC(c->W2, CC * 3 * K1 * 16);
   ARP_ALLOC(c->partial, CC * P * 3 * K1 * 16);
@@ -246,6 +248,14 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
     case ARP_OPT_CHAIN:
       if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "CHAIN must be 0, 1 or 2");
       c->chain_mode = (int)v;
+      return ARP_OK;
+    case ARP_OPT_FINE_SCHEME:
+      if (v != 0.0 && v != 1.0) return fail(c, ARP_EINVAL, "FINE_SCHEME must be 0 (ETDRK4) or 1 (Strang)");
+      c->fine_scheme = (int)v;
+      return ARP_OK;
+    case ARP_OPT_COARSE_SCHEME:
+      if (v != 0.0 && v != 1.0) return fail(c, ARP_EINVAL, "COARSE_SCHEME must be 0 (asymptotic) or 1 (Strang)");
+      c->coarse_scheme = (int)v;
       return ARP_OK;
     case ARP_OPT_FINE_BLOCK:
       if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1 or 2");

@@ -121,6 +121,7 @@ arp_status coarse_avg(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t
 }
 
 arp_status coarse_step(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
+  if (c->coarse_scheme == 1) return launch_strang_sweep(c, in, out, batch, true, s);
   for (int b0 = 0; b0 < batch; b0 += c->cchunk) {
     const int nb = batch - b0 < c->cchunk ? batch - b0 : c->cchunk;
     const size_t off = (size_t)b0 * 3 * c->H;

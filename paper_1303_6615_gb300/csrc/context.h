@@ -39,6 +39,7 @@ struct arp_ctx {
   float* weight32 = nullptr;
   double* dhalf = nullptr;       // [K1] e^{-nu k^4 dT/2}
   arp::cd* gphase = nullptr;     // [3][K1] e^{-i omega dT/eps}
+  arp::cd* strang_h64 = nullptr; // [3][K1] e^{lambda dT/2} (the Strang coarse step's half steps)
 
   // workspaces (sized for `cchunk` states)
   arp::cd* W = nullptr;          // [cchunk][3][K1] eigen, FP64
@@ -60,6 +61,8 @@ struct arp_ctx {
   int skip_arrival = 0;          // one-shot failure-detection test hook
   int chain_mode = 0;            // ARP_OPT_CHAIN
   int fine_block = 0;            // ARP_OPT_FINE_BLOCK: 0 per-size default, 1 = N/4, 2 = N/2 threads
+  int fine_scheme = 0;           // ARP_OPT_FINE_SCHEME: 0 ETDRK4, 1 Strang splitting
+  int coarse_scheme = 0;         // ARP_OPT_COARSE_SCHEME: 0 asymptotic (Algorithm 2), 1 Strang step of dT
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;
 
@@ -78,6 +81,10 @@ arp_status ensure_tables(arp_ctx* c, cudaStream_t s);
 
 // fine.cu: F applied to `batch` physical states.
 arp_status launch_fine(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
+// strang64.cu: `steps` Strang steps of size h per state (coarse: one step of
+// size dT), and standard parareal's serial chain with the Strang coarse step.
+arp_status launch_strang_sweep(arp_ctx* c, const cd* in, cd* out, int batch, bool coarse, cudaStream_t s);
+arp_status launch_strang_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
 
 // coarse.cu
 //   to_eigen: W[b] = (dhalf if use_dhalf) * R^H u[b]

@@ -72,6 +72,7 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   // barrier counter and status word start at zero whichever kernel runs
   arp_status r = check_cuda(c, cudaMemsetAsync(c->sync, 0, 4 * sizeof(unsigned), s), "chain: status reset");
   if (r != ARP_OK) return r;
+  if (c->coarse_scheme == 1) return launch_strang_chain(c, c->U, c->Gc, V, s);
   r = ARP_EINVAL;
   if (c->chain_mode == 0 && !c->skip_arrival) {
     r = launch_cluster_chain(c, c->U, c->Ge, V ? c->VT : nullptr, s);

@@ -74,7 +74,7 @@ extern "C" arp_status arp_coarse_avg_static(int N, double eps, double dT, int M,
   // tables, in the order below; then per-state workspace: W [3][K1] and partials [P][3][K1]
   const size_t sizes[] = {K1 * 8,  K1 * 8,          K1 * 4,          K1 * 4,      18 * K1 * 16, 18 * K1 * 8, 3 * K1 * 8,
                           Ns * 16, Ns * 8,          Ms * 3 * K1 * 16, Ms * 3 * K1 * 8, Ms * 8,     Ms * 4,      K1 * 8,
-                          3 * K1 * 16};
+                          3 * K1 * 16, 3 * K1 * 16};
   size_t tables = 0;
   for (size_t z : sizes) tables += align256(z);
   const size_t per_state = 3 * K1 * 16 * (1 + P);
@@ -104,6 +104,7 @@ extern "C" arp_status arp_coarse_avg_static(int N, double eps, double dT, int M,
   c.weight32 = reinterpret_cast<float*>(carve(sizes[12]));
   c.dhalf = reinterpret_cast<double*>(carve(sizes[13]));
   c.gphase = reinterpret_cast<cd*>(carve(sizes[14]));
+  c.strang_h64 = reinterpret_cast<cd*>(carve(sizes[15]));
   c.W = reinterpret_cast<cd*>(carve((size_t)chunk * 3 * K1 * 16));
   c.partial = reinterpret_cast<cd*>(carve((size_t)chunk * P * 3 * K1 * 16));
   c.slices = chunk;

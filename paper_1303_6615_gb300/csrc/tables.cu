@@ -180,8 +180,10 @@ __global__ void phase_kernel(int M, int K1, double s, double T0, cd* ph64, cf* p
   ph32[base + 1 * K1 + k] = {1.0f, 0.0f};
 }
 
-// dhalf[k] = e^{-nu k^4 dT/2}; gphase[b][k] = e^{-i omega dT/eps}.
-__global__ void coarse_consts_kernel(int K1, double s, double nu, double dT, double inv_eps, double* dhalf, cd* gph) {
+// dhalf[k] = e^{-nu k^4 dT/2}; gphase[b][k] = e^{-i omega dT/eps};
+// sth[b][k] = e^{lambda dT/2} = dhalf[k] e^{-i omega dT/(2 eps)}.
+__global__ void coarse_consts_kernel(int K1, double s, double nu, double dT, double inv_eps, double* dhalf, cd* gph,
+                                     cd* sth) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K1) return;
   const double k4 = (double)k * (double)k * (double)k * (double)k;
@@ -192,6 +194,12 @@ __global__ void coarse_consts_kernel(int K1, double s, double nu, double dT, dou
   gph[2 * K1 + k] = {cs, -sn};
   gph[0 * K1 + k] = {cs, sn};
   gph[1 * K1 + k] = {1.0, 0.0};
+  double sh, ch;
+  sincos(0.5 * arg, &sh, &ch);
+  const double d = dhalf[k];
+  sth[2 * K1 + k] = {d * ch, -d * sh};
+  sth[0 * K1 + k] = {d * ch, d * sh};
+  sth[1 * K1 + k] = {d, 0.0};
 }
 
 }  // namespace
@@ -207,7 +215,8 @@ arp_status build_tables(arp_ctx* c, cudaStream_t st) {
   etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32);
   weights_kernel<<<1, 256, 0, st>>>(c->M, c->weight64, c->weight32);
   phase_kernel<<<dim3((c->K1 + tb - 1) / tb, c->M), tb, 0, st>>>(c->M, c->K1, s, T0, c->phase64, c->phase32);
-  coarse_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->nu, c->dT, inv_eps, c->dhalf, c->gphase);
+  coarse_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->nu, c->dT, inv_eps, c->dhalf, c->gphase,
+                                                               c->strang_h64);
   arp_status r = check_cuda(c, cudaGetLastError(), "table kernels");
   if (r != ARP_OK) return r;
   c->tables_dirty = false;
