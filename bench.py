@@ -64,11 +64,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve"], default="headline",
+    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper"],
+                    default="headline",
                     help="headline: the contract line (default); tts: time to 1e-5 relative error against the "
-                         "oracle's serial fine solution, FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
+                         "serial fine solution (FP64 sweeps on the GPU), FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
                          "batched: 1024 uneven instances in one batch vs the FP64 path one instance at a time; "
-                         "serve: Poisson request streams through the continuous-batching server")
+                         "serve: Poisson request streams through the continuous-batching server; paper: the "
+                         "experiments of Sec. 6.2 (Eq. 6.4 initial condition, eps = 1e-2, 1e-1, 1), asymptotic "
+                         "and standard parareal")
     ap.add_argument("--instances", type=int, default=1024)
     return ap.parse_args()
 
@@ -341,23 +344,29 @@ def _parseval(a):
 
 def run_tts(args) -> dict:
     """Time to the first parareal iterate within 1e-5 (max over slices of the relative
-    L2 error) of the serial fine solution computed by the FP64 oracle, for the FP32-bulk
-    and the plain FP64 path, one instance each, end to end through the C ABI with host
-    buffers (u0 in; predictor and iterations; all slices out)."""
+    L2 error) of the serial fine solution, for the FP32-bulk and the plain FP64 path,
+    one instance each, end to end through the C ABI with host buffers (u0 in;
+    predictor and iterations; all slices out).  The serial fine solution comes from
+    the FP64 fine sweep chained slice by slice on the GPU (held to the FP64 oracle
+    within 1e-10 by the GPU tests); it is computed once, untimed."""
     import numpy as np
     import torch
 
-    from oracle import rsw as o
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
     w = WORKLOAD
-    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
-    t0 = time.perf_counter()
-    ref = o.serial_fine(w.initial_state(), p, w.slices)
-    t_ref = time.perf_counter() - t0
     H = w.n_grid // 2 + 1
-    out = {"mode": "tts", "workload": w.name, "target": 1e-5, "reference": "FP64 oracle serial fine solution",
+    t0 = time.perf_counter()
+    ser = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
+    ser[0] = torch.from_numpy(w.initial_state()).cuda()
+    with b.Solver(w.n_grid, w.eps, w.nu, 1, w.dT, w.dt, w.m_quad) as s:
+        for n in range(w.slices):
+            b.arp_fine_batch(s.ctx, ser[n:n + 1], ser[n + 1:n + 2])
+    ref = ser.cpu().numpy()
+    t_ref = time.perf_counter() - t0
+    out = {"mode": "tts", "workload": w.name, "target": 1e-5,
+           "reference": "serial fine solution, FP64 sweeps chained slice by slice on the GPU",
            "reference_seconds": t_ref}
     u0h = torch.from_numpy(w.initial_state()).pin_memory()
     Uh = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128).pin_memory()
@@ -390,24 +399,130 @@ def run_tts(args) -> dict:
     return out
 
 
-def run_precision(args) -> dict:
-    """Precision sweep on the N=1024 instance (eps=1e-4, 512 slices, 1954 fine steps,
-    M=128): per-field relative L2 error of one fine sweep against the oracle and the
-    mean-height drift, for FP64 and FP32 bulk; then full-size parareal, FP32 against FP64
-    (iterates k = 0..3) and the time per iteration of each."""
+def eq51_speedup(slices, fine_steps_per_slice, iters, tau_f=1.0, tau_c=1.0):
+    """Eq. 5.1's complexity model: serial fine cost over the cost of `iters`
+    parareal iterations (each a parallel fine sweep and a serial coarse chain)
+    plus the coarse predictor."""
+    N, M = slices, fine_steps_per_slice
+    return tau_f * N * M / (iters * (tau_f * M + tau_c * N + tau_c) + tau_c * N)
+
+
+def _linf_rel(U, ref, n_grid):
+    """max over slices of max_{x, field} |U - ref| / max_{x, field} |ref| (physical L-inf)."""
+    import numpy as np
+    d = np.fft.irfft(U * n_grid, n=n_grid, axis=-1)
+    r = np.fft.irfft(ref * n_grid, n=n_grid, axis=-1)
+    return float(np.max(np.max(np.abs(d - r), axis=(-2, -1)) / np.max(np.abs(r), axis=(-2, -1))))
+
+
+def run_paper(args) -> dict:
+    """Sec. 6.2's experiments on the GPU (FP64): the initial condition of Eq. 6.4,
+    eps = 1e-2, 1e-1, 1 with the printed steps, window and nodes; the asymptotic
+    method (ETDRK4 fine solver) and standard parareal with the Strang coarse step
+    at the printed coarse steps; max relative L-inf error against the serial fine
+    solution per iteration k = 0..5; Eq. 5.1's estimated speedup with equal step
+    costs (the paper's assumption) and with the step costs measured here, and the
+    measured ratio of serial fine time to the time of the predictor plus 5
+    iterations."""
     import numpy as np
     import torch
 
-    from oracle import rsw as o
+    import rsw_inputs as ri
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    kmax = 5
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def serial_fine(e, dT, slices, u0):
+        """u(n dT), n = 0..slices, by one-state fine sweeps chained on the GPU; and the sweep time per step."""
+        H = e.n_grid // 2 + 1
+        out = torch.empty((slices + 1, 3, H), dtype=torch.complex128, device="cuda")
+        out[0] = torch.from_numpy(u0).cuda()
+        with b.Solver(e.n_grid, e.eps, e.nu, 1, dT, e.dt, e.m_quad) as s:
+            b.arp_fine_batch(s.ctx, out[0:1], out[1:2])  # warm-up
+            e0, e1 = events()
+            e0.record()
+            for n in range(slices):
+                b.arp_fine_batch(s.ctx, out[n:n + 1], out[n + 1:n + 2])
+            e1.record()
+            torch.cuda.synchronize()
+        steps = fine_steps(dT, e.dt)
+        return out.cpu().numpy(), e0.elapsed_time(e1) / 1e3, steps
+
+    def parareal(e, dT, slices, u0, coarse, window=None):
+        H = e.n_grid // 2 + 1
+        U = torch.empty((slices + 1, 3, H), dtype=torch.complex128, device="cuda")
+        its, times = [], []
+        with b.Solver(e.n_grid, e.eps, e.nu, slices, dT, e.dt, e.m_quad, T0=window) as s:
+            b.arp_set_option(s.ctx, b.ARP_OPT_COARSE_SCHEME, coarse)
+            for rep in range(2):  # the first pass warms up, the second is timed
+                b.arp_set_initial(s.ctx, torch.from_numpy(u0).cuda())
+                its, times = [], []
+                for _ in range(kmax + 1):
+                    e0, e1 = events()
+                    e0.record()
+                    b.arp_parareal_iterate(s.ctx)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1) / 1e3)
+                    b.arp_get_slices(s.ctx, U)
+                    its.append(U.cpu().numpy())
+        return its, times
+
+    out = {"mode": "paper", "precision": "fp64", "fine": "ETDRK4", "experiments": []}
+    for e in ri.PAPER_EXPERIMENTS:
+        u0 = ri.paper_initial_state(e.n_grid)
+        ref, t_serial, steps = serial_fine(e, e.dT, e.slices, u0)
+        its, times = parareal(e, e.dT, e.slices, u0, 0, e.window)
+        errs = [_linf_rel(U[1:], ref[1:], e.n_grid) for U in its]
+        tau_f = t_serial / (e.slices * steps)          # one fine step of one slice
+        tau_c = times[0] / e.slices                     # one link of the predictor's chain
+        row = {"name": e.name, "eps": e.eps, "dT": e.dT, "dt": e.dt, "window_fast_time": e.window,
+               "M": e.m_quad, "slices": e.slices, "N": e.n_grid, "fine_steps_per_slice": steps,
+               "asymptotic": {"errors_per_k": errs, "seconds_per_call": times,
+                              "eq51_equal_costs": None, "eq51_measured_costs": None},
+               "tau_f_us": tau_f * 1e6, "tau_c_us": tau_c * 1e6, "serial_fine_seconds": t_serial}
+        row["asymptotic"]["eq51_equal_costs"] = eq51_speedup(e.slices, steps, kmax)
+        row["asymptotic"]["eq51_measured_costs"] = eq51_speedup(e.slices, steps, kmax, tau_f, tau_c)
+        row["asymptotic"]["measured_speedup"] = t_serial / sum(times)
+        row["standard"] = []
+        for dT in e.standard_dT:
+            S = int(round(e.t_end / dT))
+            ref_s, t_ser_s, steps_s = serial_fine(e, dT, S, u0)
+            its_s, times_s = parareal(e, dT, S, u0, 1)
+            errs_s = [_linf_rel(U[1:], ref_s[1:], e.n_grid) for U in its_s]
+            tc_s = times_s[0] / S
+            tf_s = t_ser_s / (S * steps_s)
+            row["standard"].append({"dT": dT, "slices": S, "fine_steps_per_slice": steps_s, "errors_per_k": errs_s,
+                                    "seconds_per_call": times_s, "tau_c_us": tc_s * 1e6,
+                                    "eq51_equal_costs": eq51_speedup(S, steps_s, kmax),
+                                    "eq51_measured_costs": eq51_speedup(S, steps_s, kmax, tf_s, tc_s),
+                                    "measured_speedup": t_ser_s / sum(times_s)})
+        out["experiments"].append(row)
+        print(json.dumps({"done": e.name, "errors": errs}), file=sys.stderr, flush=True)
+    return out
+
+
+def run_precision(args) -> dict:
+    """Precision sweep on the N=1024 instance (eps=1e-4, 512 slices, 1954 fine steps,
+    M=128): per-field relative L2 error of one FP32-bulk fine sweep against the FP64
+    path (which the GPU tests hold to the FP64 oracle within 1e-10) and the mean-height
+    drift of both; then full-size parareal, FP32 against FP64 (iterates k = 0..3) and
+    the time per iteration of each."""
+    import numpy as np
+    import torch
+
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
     w = ri.SWEEP_N1024
-    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
     H = w.n_grid // 2 + 1
     x = ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, 3, 500) * 64.0
-    ref = o.fine_propagate(x, p)
-    out = {"mode": "precision", "workload": w.name, "fine_sweep_vs_oracle": {}, "parareal_fp32_vs_fp64": {}}
+    ref = None
+    out = {"mode": "precision", "workload": w.name, "fine_sweep_vs_fp64": {}, "parareal_fp32_vs_fp64": {}}
     fields = ("v1", "v2", "h")
     iterates = {}
     for name, prec in (("fp64", b.ARP_FP64), ("fp32", b.ARP_FP32)):
@@ -416,10 +531,12 @@ def run_precision(args) -> dict:
             y = torch.empty_like(xin)
             b.arp_fine_batch(s.ctx, xin, y)
             got = y.cpu().numpy()
+            if ref is None:
+                ref = got  # the FP64 sweep (first in this loop)
             rel = {f: float(np.max(np.linalg.norm(got[:, i] - ref[:, i], axis=-1) / np.linalg.norm(ref[:, i], axis=-1)))
                    for i, f in enumerate(fields)}
             drift = float(np.max(np.abs(got[:, 2, 0] - x[:, 2, 0].real) / np.abs(x[:, 2, 0].real)))
-            out["fine_sweep_vs_oracle"][name] = {"rel_l2": rel, "mean_height_drift": drift}
+            out["fine_sweep_vs_fp64"][name] = {"rel_l2": rel, "mean_height_drift": drift}
             b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
             U = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
             its, ms = [], []
@@ -586,7 +703,8 @@ def main():
         if rank == 0:
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-            res = {"tts": run_tts, "precision": run_precision, "batched": run_batched, "serve": run_serve}[args.mode](args)
+            res = {"tts": run_tts, "precision": run_precision, "batched": run_batched, "serve": run_serve,
+                   "paper": run_paper}[args.mode](args)
             print(json.dumps(res), flush=True)
         return
     if args.impl == "reference":

@@ -17,6 +17,10 @@ Spectral layout of a state (shared by every public buffer of the library):
   physical field is u_f(x_j) = sum_{k=-N/2+1}^{N/2} u[f, k] e^{i k x_j} with
   x_j = 2 pi j / N and u[f, -k] = conj(u[f, k]) (real fields).
 
+The deterministic initial condition of the paper's experiments (Sec. 6.2,
+Eq. 6.4) is provided by `paper_initial_state`: its samples on the grid and
+their discrete Fourier coefficients, nothing else.
+
 Initial spectra: the drawn values are discrete Fourier coefficients in the
 unnormalised convention of FFT libraries, X_k = sum_j u(x_j) e^{-i k x_j}, so
 the stored coefficient is u[f, k] = X_k / N.  For 0 < k <= cutoff, Re X_k and
@@ -144,3 +148,69 @@ def uneven_instances(count: int, seed: int = 1000):
         slices = (32, 64, 128)[g.next_u64() % 3]
         out.append(Workload(f"uneven-{i}", n_grid, eps, 1e-4, 1.0, slices, eps / 10.0, 32, 5, 8, 16.0, seed + i))
     return out
+
+
+def paper_height_profile(x: np.ndarray) -> np.ndarray:
+    """The bracket of Eq. 6.4 (Sec. 6.2): two Gaussian-windowed sines."""
+    a = x - math.pi / 2.0
+    b = x - math.pi
+    return np.exp(-4.0 * a * a) * np.sin(3.0 * a) + np.exp(-2.0 * b * b) * np.sin(8.0 * b)
+
+
+def paper_height_constants(fine: int = 1 << 16) -> tuple[float, float]:
+    """c1, c0 of Eq. 6.4: h = c1 f + c0 with zero mean over [0, 2 pi) and
+    max |h| = 1, both evaluated on `fine` equispaced points."""
+    x = 2.0 * math.pi * np.arange(fine) / fine
+    f = paper_height_profile(x)
+    mean = float(np.mean(f))
+    c1 = 1.0 / float(np.max(np.abs(f - mean)))
+    return c1, -c1 * mean
+
+
+def paper_initial_state(n_grid: int) -> np.ndarray:
+    """Sec. 6.2's initial condition on N points: v1 = v2 = 0 and h of Eq. 6.4,
+    stored as u[2, k] = X_k / N from the samples h(x_j), shape (3, N/2+1)."""
+    if n_grid < 2 or n_grid & (n_grid - 1):
+        raise ValueError("grid size must be a power of two")
+    c1, c0 = paper_height_constants()
+    x = 2.0 * math.pi * np.arange(n_grid) / n_grid
+    h = c1 * paper_height_profile(x) + c0
+    u = np.zeros((3, half_bins(n_grid)), dtype=np.complex128)
+    u[2] = np.fft.rfft(h) / n_grid
+    return u
+
+
+@dataclass(frozen=True)
+class PaperExperiment:
+    """One experiment of Sec. 6.2: the asymptotic method's dT, dt, fast-time
+    averaging window T0 and M (nodes), its number of slices, and the coarse steps of the
+    standard-parareal comparison runs (Strang coarse solver, same dt, same
+    horizon).  Grid, horizons and the conflicting printed values are readings
+    (see the experiment tables)."""
+    name: str
+    eps: float
+    dT: float
+    dt: float
+    window: float
+    m_quad: int
+    slices: int
+    standard_dT: tuple
+    n_grid: int = 128
+    nu: float = 1e-4
+
+    @property
+    def t_end(self) -> float:
+        return self.slices * self.dT
+
+
+# eps = 1e-2: dT = 50 eps, dt = eps/25, averaging over 150 eps of physical
+# time, M = 450; standard parareal with dT = 4 eps and 5 eps.  eps = 1e-1:
+# dT = 3 eps, dt = eps/50, 5 eps of physical time, M = 10, 150 slices; standard
+# with dT = eps and 2 eps.  eps = 1: dT = 3/10, dt = 1/200, 3/10 of physical
+# time, M = 10, 60 slices; standard with dT = 3/10 and 4/10.  `window` is the
+# fast-time window (the physical one divided by eps).
+PAPER_EXPERIMENTS = (
+    PaperExperiment("paper-eps1e-2", 1e-2, 0.5, 1e-2 / 25, 150.0, 450, 128, (0.04, 0.05)),
+    PaperExperiment("paper-eps1e-1", 1e-1, 0.3, 1e-1 / 50, 5.0, 10, 150, (0.1, 0.2)),
+    PaperExperiment("paper-eps1", 1.0, 0.3, 1.0 / 200, 0.3, 10, 60, (0.3, 0.4)),
+)

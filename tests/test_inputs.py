@@ -50,3 +50,25 @@ def test_workloads():
     assert all(1e-4 <= i.eps <= 1e-2 for i in insts)
     assert {i.slices for i in insts} <= {32, 64, 128}
     assert [i.seed for i in insts[:3]] == [1000, 1001, 1002]
+
+
+def test_paper_initial_condition():
+    # Eq. 6.4: v1 = v2 = 0, h of zero mean with max |h| = 1; the stored
+    # coefficients resynthesise the samples, and the constants hold on a grid
+    # finer than the one they were fixed on (to 1e-8: the profile is periodic
+    # only up to its Gaussian tails, about 5e-5 at the ends of [0, 2 pi)).
+    import math
+    c1, c0 = ri.paper_height_constants()
+    x = 2 * math.pi * np.arange(1 << 18) / (1 << 18)
+    h = c1 * ri.paper_height_profile(x) + c0
+    assert abs(h.mean()) < 1e-8
+    assert abs(np.abs(h).max() - 1.0) < 1e-6
+    u = ri.paper_initial_state(64)
+    assert np.all(u[:2] == 0)
+    xs = 2 * math.pi * np.arange(64) / 64
+    k = np.arange(33)
+    coef = np.where(k == 0, 1.0, 2.0)
+    synth = np.array([np.sum(coef * (u[2] * np.exp(1j * k * xj)).real) for xj in xs])
+    synth -= (u[2, 32] * np.exp(1j * 32 * xs)).real   # the Nyquist bin counts once
+    np.testing.assert_allclose(synth, c1 * ri.paper_height_profile(xs) + c0, atol=1e-12)
+    assert [e.name for e in ri.PAPER_EXPERIMENTS] == ["paper-eps1e-2", "paper-eps1e-1", "paper-eps1"]
