@@ -35,6 +35,8 @@ Functions and the passages they follow:
   nbar                 finite, discretised average of Eq. 2.1 (Algorithm 1)
   coarse_step          asymptotic slow solver (Algorithm 2)
   strang_step/strang_propagate   Strang-splitting fine solver (Algorithm 3)
+  ifrk4_step/ifrk4_propagate     integrating-factor RK4, the comparator of Sec. 6.2
+                       (the integrating factor method of Kassam & Trefethen)
   coarse_step_strang   one Strang step over dT: the coarse solver of standard
                        parareal on the full equation (Sec. 6.2)
   parareal             the iteration of Eq. 3.1 (Algorithm 4)
@@ -346,6 +348,36 @@ def strang_propagate(u: np.ndarray, p: Params, nl: NonlinearFn = nonlinear,
     u = project(u, p.n_grid)
     for _ in range(steps):
         u = strang_step(u, p, h, nl)
+    return u
+
+
+def ifrk4_step(u: np.ndarray, p: Params, h: float, nl: NonlinearFn = nonlinear) -> np.ndarray:
+    """One integrating-factor RK4 step: classical RK4 applied to
+    v = e^{-t A} u, A = -L/eps + D, so that v' = e^{-t A} N(e^{t A} v), mapped
+    back (E = e^{hA}, E2 = e^{hA/2}):
+        k1 = N(u);  k2 = N(E2 (u + h/2 k1));  k3 = N(E2 u + h/2 k2);
+        k4 = N(E u + h E2 k3);
+        u+ = E u + h/6 (E k1 + 2 E2 (k2 + k3) + k4)."""
+    E2 = _linear_half(p, h)
+    E = _linear_half(p, 2.0 * h)
+    n = p.n_grid
+    k1 = nl(u, n)
+    k2 = nl(_apply(E2, u + (h / 2.0) * k1), n)
+    k3 = nl(_apply(E2, u) + (h / 2.0) * k2, n)
+    k4 = nl(_apply(E, u) + h * _apply(E2, k3), n)
+    return _apply(E, u) + (h / 6.0) * (_apply(E, k1) + 2.0 * _apply(E2, k2 + k3) + k4)
+
+
+def ifrk4_propagate(u: np.ndarray, p: Params, nl: NonlinearFn = nonlinear,
+                    steps: Optional[int] = None) -> np.ndarray:
+    """The integrating-factor RK4 fine propagator over one coarse interval dT."""
+    if steps is None:
+        steps, h = fine_steps(p.dT, p.dt)
+    else:
+        h = p.dT / steps
+    u = project(u, p.n_grid)
+    for _ in range(steps):
+        u = ifrk4_step(u, p, h, nl)
     return u
 
 

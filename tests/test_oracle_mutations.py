@@ -65,8 +65,19 @@ def _bad_strang_stage_from_u(u, p, h, nl=None):
     return rsw._apply(E2, w + h * k2)
 
 
+def _bad_ifrk4_stage(u, p, h, nl=None):
+    nl = nl or rsw.nonlinear
+    E2 = rsw.linear_matrices(p, h / 2.0)
+    E = rsw.linear_matrices(p, h)
+    k1 = nl(u, p.n_grid)
+    k2 = nl(rsw._apply(E2, u + h / 2 * k1), p.n_grid)
+    k3 = nl(u + h / 2 * k2, p.n_grid)                    # third stage without the half-step factor
+    k4 = nl(rsw._apply(E, u) + h * rsw._apply(E2, k3), p.n_grid)
+    return rsw._apply(E, u) + h / 6 * (rsw._apply(E, k1) + 2 * rsw._apply(E2, k2 + k3) + k4)
+
+
 _orig = {name: getattr(rsw, name) for name in
-         ("nonlinear", "phi123", "etdrk4_coefficients", "expL", "_apply", "quadrature", "strang_step")}
+         ("nonlinear", "phi123", "etdrk4_coefficients", "expL", "_apply", "quadrature", "strang_step", "ifrk4_step")}
 
 CASES = [
     ("nonlinear", _bad_nl_sign, tm.test_nonlinearity_analytic_case, ()),
@@ -79,6 +90,7 @@ CASES = [
     ("quadrature", _bad_quadrature, tc.test_quadrature_weights_sum_to_one, (32,)),
     ("strang_step", _bad_strang_one_half_step, ts.test_strang_linear_part_is_exact, ()),
     ("strang_step", _bad_strang_stage_from_u, ts.test_strang_second_order_convergence, ()),
+    ("ifrk4_step", _bad_ifrk4_stage, ts.test_ifrk4_fourth_order_and_invariants, ()),
 ]
 
 

@@ -89,3 +89,46 @@ def test_standard_parareal_error_falls_with_iterations():
     res = o.parareal(u0, p, S, k_max=4, G=lambda x: o.coarse_step_strang(x, p))
     err = [float(np.max(o.physical_linf(U - ser, 32) / o.physical_linf(ser, 32))) for U in res.iterates]
     assert all(err[i + 1] < err[i] for i in range(len(err) - 1)), err
+
+
+# ----------------------------------------------------------- integrating-factor RK4
+
+def test_ifrk4_linear_part_is_exact():
+    p = o.Params(32, 0.01, 1e-3, 0.0625, 1e-3, 8)
+    u0 = _state(32)
+    zero = lambda u, n: np.zeros_like(u)
+    got = o.ifrk4_propagate(u0, p, nl=zero)
+    for k in range(p.H):
+        A = -o.L_symbol(float(k)) / p.eps - p.nu * k ** 4 * np.eye(3)
+        np.testing.assert_allclose(got[:, k], expm(p.dT * A) @ o.project(u0, 32)[:, k],
+                                   atol=1e-13 * np.max(np.abs(u0)))
+
+
+def test_ifrk4_reduces_to_classical_rk4():
+    # eps = inf and nu = 0: the integrating factor is the identity.
+    p = o.Params(32, math.inf, 0.0, 0.01, 0.01, 8)
+    x = o.project(_state(32, amp=20.0), 32)
+    h = 0.01
+    N = lambda y: o.nonlinear(y, 32)
+    k1 = N(x)
+    k2 = N(x + h / 2 * k1)
+    k3 = N(x + h / 2 * k2)
+    k4 = N(x + h * k3)
+    ref = x + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    np.testing.assert_allclose(o.ifrk4_step(x, p, h), ref, atol=1e-15 * np.max(np.abs(ref)))
+
+
+def test_ifrk4_fourth_order_and_invariants():
+    n = 32
+    p = o.Params(n, 0.05, 1e-3, 0.05, 0.01, 8)
+    u0 = _state(n, amp=30.0)
+    ref = o.fine_propagate(u0, p, steps=512)
+    errs = [o.parseval_norm(o.ifrk4_propagate(u0, p, steps=s) - ref) for s in (8, 16, 32, 64)]
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(slopes) > 3.5, (errs, slopes)
+    q = o.Params(32, 0.01, 1e-4, 0.0625, 1e-3, 8)
+    f = o.ifrk4_propagate(u0, q)
+    assert abs(f[2, 0] - u0[2, 0]) < 1e-14 * np.max(np.abs(u0))
+    g0 = _geostrophic_state(32, 4)
+    decay = np.exp(-q.nu * np.arange(q.H) ** 4 * q.dT)
+    np.testing.assert_allclose(o.ifrk4_propagate(g0, q), decay * g0, atol=1e-13)
