@@ -76,8 +76,10 @@ typedef enum {
                               differ in the last bits (default 0) */
   ARP_OPT_FINE_SCHEME = 8,  /* fine propagator F: 0 = ETDRK4 (Cox & Matthews, default), 1 = Strang
                                splitting (Algorithm 3: exact linear half steps around a midpoint
-                               step of N, steps of size h = dT/ceil(dT/dt)); used by
-                               arp_fine_batch and the parareal iteration */
+                               step of N), 2 = integrating-factor RK4 (classical RK4 on
+                               e^{-t(-L/eps+D)} u, the comparator of Sec. 6.2); steps of size
+                               h = dT/ceil(dT/dt); used by arp_fine_batch and the parareal
+                               iteration */
   ARP_OPT_COARSE_SCHEME = 9,  /* coarse propagator G: 0 = the asymptotic slow solver
                                  (Algorithm 2, default), 1 = one Strang step of size dT of the
                                  full equation (standard parareal, Sec. 6.2); used by

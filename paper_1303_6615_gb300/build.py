@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libarp.so")
 
 SOURCES = ["api.cu", "tables.cu", "fine64.cu", "fine32.cu", "chain64.cu", "chain32.cu", "coarse.cu", "strang64.cu",
-           "strang32.cu",
+           "strang32.cu", "ifrk64.cu", "ifrk32.cu",
            "parareal.cu", "static_avg.cu",
            "batch.cu", "batch64.cu", "batch32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -250,7 +250,8 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       c->chain_mode = (int)v;
       return ARP_OK;
     case ARP_OPT_FINE_SCHEME:
-      if (v != 0.0 && v != 1.0) return fail(c, ARP_EINVAL, "FINE_SCHEME must be 0 (ETDRK4) or 1 (Strang)");
+      if (v != 0.0 && v != 1.0 && v != 2.0)
+        return fail(c, ARP_EINVAL, "FINE_SCHEME must be 0 (ETDRK4), 1 (Strang) or 2 (integrating-factor RK4)");
       c->fine_scheme = (int)v;
       return ARP_OK;
     case ARP_OPT_COARSE_SCHEME:

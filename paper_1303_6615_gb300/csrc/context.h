@@ -61,7 +61,7 @@ struct arp_ctx {
   int skip_arrival = 0;          // one-shot failure-detection test hook
   int chain_mode = 0;            // ARP_OPT_CHAIN
   int fine_block = 0;            // ARP_OPT_FINE_BLOCK: 0 per-size default, 1 = N/4, 2 = N/2 threads
-  int fine_scheme = 0;           // ARP_OPT_FINE_SCHEME: 0 ETDRK4, 1 Strang splitting
+  int fine_scheme = 0;           // ARP_OPT_FINE_SCHEME: 0 ETDRK4, 1 Strang splitting, 2 integrating-factor RK4
   int coarse_scheme = 0;         // ARP_OPT_COARSE_SCHEME: 0 asymptotic (Algorithm 2), 1 Strang step of dT
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;

@@ -13,6 +13,11 @@
 // After each transform a single pass over wavenumbers unpacks N, applies the
 // ETDRK4 combination for the stage, and packs the next stage's input.
 //
+// SCHEME 1 instead runs integrating-factor RK4 (the comparator of Sec. 6.2):
+// classical RK4 on v = e^{-t lambda} a, with the same tables E, E2:
+//     x2 = E2 (u + h/2 N(u));  x3 = E2 u + h/2 N(x2);  x4 = E u + h E2 N(x3)
+//     u+ = E u + h/6 (E N(u) + 2 E2 (N(x2) + N(x3)) + N(x4)).
+//
 // FP32 path: transforms, products, stage values a1..a3 and the N(.) terms are
 // FP32, but the state u and the running update sum are carried as float pairs
 // hi + lo and multiplied by E = e^{h lambda} held as a float pair too, so the
@@ -46,7 +51,12 @@ struct FineTabs {
   const T* ss;
   const double* is64;
   const double* ss64;
+  double h;        // the step (integrating-factor RK4 weights)
 };
+
+// Fine time-stepping schemes sharing the four-evaluation step structure.
+constexpr int kSchemeEtdrk4 = 0;
+constexpr int kSchemeIfrk4 = 1;
 
 template <int LOGN> struct FineBlock {
   static constexpr int N = 1 << LOGN;
@@ -104,7 +114,7 @@ __device__ __forceinline__ void store_phys64(cd* __restrict__ dst, int H, int k,
   }
 }
 
-template <typename T, int LOGN, int BLOCK>
+template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
 __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
                                           const FineTabs<T>& tb, int slice) {
   constexpr int N = 1 << LOGN;
@@ -122,6 +132,7 @@ __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restr
   cpx<T>* A1 = NU + 3 * K1;
   cpx<T>* ACC = A1 + 3 * K1;
   constexpr bool kPair = std::is_same<T, float>::value;
+  static_assert(!(kPair && SCHEME != kSchemeEtdrk4), "the FP32 schemes run in fine_f32_body");
   cpx<T>* ULO = ACC + 3 * K1;                       // FP32 path only
   cpx<T>* ACCLO = ULO + (kPair ? 3 * K1 : 0);       // FP32 path only
   T* IS = reinterpret_cast<T*>(ACC + 3 * K1 + (kPair ? 6 * K1 : 0));
@@ -196,6 +207,21 @@ __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restr
               nx[q] = (stage == 1) ? ldgc(e.E2 + i) * U[i] + ldgc(e.Q + i) * bn[q]
                                    : ldgc(e.E2 + i) * A1[i] + ldgc(e.Q + i) * ((T)2 * bn[q] - NU[i]);
             }
+          } else if constexpr (SCHEME == kSchemeIfrk4) {
+            const T h = (T)tb.h;
+            if (stage == 0) {
+              const cpx<T> u = U[i], E = ldgc(e.E + i);
+              ACC[i] = E * u + (h / (T)6) * (E * bn[q]);
+              nx[q] = ldgc(e.E2 + i) * (u + ((T)0.5 * h) * bn[q]);
+            } else if (stage == 3) {
+              const cpx<T> u = ACC[i] + (h / (T)6) * bn[q];
+              U[i] = u;
+              nx[q] = u;
+            } else {
+              const cpx<T> E2 = ldgc(e.E2 + i), t = E2 * bn[q];
+              ACC[i] = ACC[i] + (h / (T)3) * t;
+              nx[q] = (stage == 1) ? E2 * U[i] + ((T)0.5 * h) * bn[q] : ldgc(e.E + i) * U[i] + h * t;
+            }
           } else {
             if (stage == 0) {
               const cpx<T> u = U[i];
@@ -240,10 +266,10 @@ __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restr
   }
 }
 
-template <typename T, int LOGN, int BLOCK>
+template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
 __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict__ in, cd* __restrict__ out,
                                                            int steps, FineTabs<T> tb) {
-  fine_body<T, LOGN, BLOCK>(in, out, steps, tb, blockIdx.x);
+  fine_body<T, LOGN, BLOCK, SCHEME>(in, out, steps, tb, blockIdx.x);
 }
 
 // FP32 fine sweep with the ETDRK4 state in registers: thread t owns the
@@ -257,7 +283,7 @@ struct F32Layout {
   static constexpr size_t kBytes = (size_t)lanes_and_twiddles<float>(LOGN) * sizeof(cf) + (size_t)2 * K1 * sizeof(float);
 };
 
-template <int LOGN, int BLOCK>
+template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
 __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
                                               const FineTabs<float>& tb, int slice) {
   using T = float;
@@ -314,7 +340,32 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int i = q * K1 + k;
-          if (stage == 0) {
+          if constexpr (SCHEME == kSchemeIfrk4) {
+            const float h = (float)tb.h;
+            if (stage == 0) {
+              // acc = E u (float pair) + h/6 E N(u); next: E2 (u + h/2 N(u))
+              const cf E = ldgc(e.E + i);
+              const cdf s = cdf_add(cdf_mul(E, ldgc(tb.E_lo + i), u[r][q], ulo[r][q]), (h / 6.0f) * (E * bn[q]));
+              acc[r][q] = mk<float>(s.re.hi, s.im.hi);
+              acclo[r][q] = mk<float>(s.re.lo, s.im.lo);
+              nx[q] = ldgc(e.E2 + i) * (u[r][q] + (0.5f * h) * bn[q]);
+            } else if (stage == 3) {
+              const cf t = (h / 6.0f) * bn[q];
+              const df re = df_add_f(df{acc[r][q].x, acclo[r][q].x}, t.x);
+              const df im = df_add_f(df{acc[r][q].y, acclo[r][q].y}, t.y);
+              u[r][q] = mk<float>(re.hi, im.hi);
+              ulo[r][q] = mk<float>(re.lo, im.lo);
+              nx[q] = u[r][q];
+            } else {
+              const cf E2 = ldgc(e.E2 + i), w = E2 * bn[q];
+              const cf t = (h / 3.0f) * w;
+              const df re = df_add_f(df{acc[r][q].x, acclo[r][q].x}, t.x);
+              const df im = df_add_f(df{acc[r][q].y, acclo[r][q].y}, t.y);
+              acc[r][q] = mk<float>(re.hi, im.hi);
+              acclo[r][q] = mk<float>(re.lo, im.lo);
+              nx[q] = (stage == 1) ? E2 * u[r][q] + (0.5f * h) * bn[q] : ldgc(e.E + i) * u[r][q] + h * w;
+            }
+          } else if (stage == 0) {
             nu[r][q] = bn[q];
             a1[r][q] = ldgc(e.E2 + i) * u[r][q] + ldgc(e.Q + i) * bn[q];
             const cdf s = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(tb.E_lo + i), u[r][q], ulo[r][q]), ldgc(e.f1 + i) * bn[q]);
@@ -362,10 +413,10 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
   }
 }
 
-template <int LOGN, int BLOCK>
+template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
 __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
                                                                int steps, FineTabs<float> tb) {
-  fine_f32_body<LOGN, BLOCK>(in, out, steps, tb, blockIdx.x);
+  fine_f32_body<LOGN, BLOCK, SCHEME>(in, out, steps, tb, blockIdx.x);
 }
 
 template <typename T>
@@ -375,23 +426,23 @@ template <>
 inline FineTabs<double> fine_tabs<double>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd64, c->etd64 + n, c->etd64 + 2 * n, c->etd64 + 3 * n, c->etd64 + 4 * n, c->etd64 + 5 * n},
-          nullptr, c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64};
+          nullptr, c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64, c->h};
 }
 
 template <>
 inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd32, c->etd32 + n, c->etd32 + 2 * n, c->etd32 + 3 * n, c->etd32 + 4 * n, c->etd32 + 5 * n},
-          c->E_lo32, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64};
+          c->E_lo32, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64, c->h};
 }
 
-template <typename T, int LOGN, int BLOCK>
+template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
 arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int steps, cudaStream_t s) {
   constexpr bool kF32 = std::is_same<T, float>::value;
   const size_t smem = kF32 ? F32Layout<LOGN, BLOCK>::kBytes : FineLayout<T, LOGN>::kBytes;
   const void* kern;
-  if constexpr (kF32) kern = (const void*)fine_sweep_kernel_f32<LOGN, BLOCK>;
-  else kern = (const void*)fine_sweep_kernel<T, LOGN, BLOCK>;
+  if constexpr (kF32) kern = (const void*)fine_sweep_kernel_f32<LOGN, BLOCK, SCHEME>;
+  else kern = (const void*)fine_sweep_kernel<T, LOGN, BLOCK, SCHEME>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");
   FineTabs<T> tb = fine_tabs<T>(c);
@@ -420,27 +471,27 @@ int fine_choice_f32(const arp_ctx* c) {
   else return c->fine_block == 1 ? 0 : (c->fine_block == 2 ? 1 : (FineAltDefault<LOGN>::value ? 1 : 0));
 }
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, int SCHEME = kSchemeEtdrk4>
 arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
   constexpr int B0 = FineBlock<LOGN>::value, B1 = FineBlockAlt<LOGN>::value;
   if constexpr (std::is_same<T, float>::value && B0 != B1) {
-    if (fine_choice_f32<LOGN>(c) == 1) return launch_fine_block<T, LOGN, B1>(c, in, out, batch, c->steps, s);
+    if (fine_choice_f32<LOGN>(c) == 1) return launch_fine_block<T, LOGN, B1, SCHEME>(c, in, out, batch, c->steps, s);
   }
-  return launch_fine_block<T, LOGN, B0>(c, in, out, batch, c->steps, s);
+  return launch_fine_block<T, LOGN, B0, SCHEME>(c, in, out, batch, c->steps, s);
 }
 
-template <typename T>
+template <typename T, int SCHEME = kSchemeEtdrk4>
 arp_status launch_fine_prec(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
   switch (c->logN) {
-    case 3: return launch_fine_n<T, 3>(c, in, out, batch, s);
-    case 4: return launch_fine_n<T, 4>(c, in, out, batch, s);
-    case 5: return launch_fine_n<T, 5>(c, in, out, batch, s);
-    case 6: return launch_fine_n<T, 6>(c, in, out, batch, s);
-    case 7: return launch_fine_n<T, 7>(c, in, out, batch, s);
-    case 8: return launch_fine_n<T, 8>(c, in, out, batch, s);
-    case 9: return launch_fine_n<T, 9>(c, in, out, batch, s);
-    case 10: return launch_fine_n<T, 10>(c, in, out, batch, s);
-    case 11: return launch_fine_n<T, 11>(c, in, out, batch, s);
+    case 3: return launch_fine_n<T, 3, SCHEME>(c, in, out, batch, s);
+    case 4: return launch_fine_n<T, 4, SCHEME>(c, in, out, batch, s);
+    case 5: return launch_fine_n<T, 5, SCHEME>(c, in, out, batch, s);
+    case 6: return launch_fine_n<T, 6, SCHEME>(c, in, out, batch, s);
+    case 7: return launch_fine_n<T, 7, SCHEME>(c, in, out, batch, s);
+    case 8: return launch_fine_n<T, 8, SCHEME>(c, in, out, batch, s);
+    case 9: return launch_fine_n<T, 9, SCHEME>(c, in, out, batch, s);
+    case 10: return launch_fine_n<T, 10, SCHEME>(c, in, out, batch, s);
+    case 11: return launch_fine_n<T, 11, SCHEME>(c, in, out, batch, s);
     default: return fail(c, ARP_EINVAL, "fine: unsupported grid size");
   }
 }

@@ -1,6 +1,7 @@
 """GPU parity of the Strang-splitting paths (Algorithm 3; standard parareal with
-the Strang coarse step, Sec. 6.2) through the C ABI against the FP64 oracle:
-relative L2 <= 1e-10 (FP64) and <= 1e-5 (FP32 bulk), per state."""
+the Strang coarse step, Sec. 6.2) and of the integrating-factor RK4 fine solver
+(Sec. 6.2's comparator) through the C ABI against the FP64 oracle: relative
+L2 <= 1e-10 (FP64) and <= 1e-5 (FP32 bulk), per state."""
 import numpy as np
 import pytest
 
@@ -76,9 +77,9 @@ def test_strang_coarse_step_and_options():
             # the time average itself does not depend on the coarse scheme
             avg = _call(b.arp_coarse_avg, s, x)
             assert per_state_rel_l2(avg, o.nbar(x, p)).max() <= tol
-            for key in (b.ARP_OPT_FINE_SCHEME, b.ARP_OPT_COARSE_SCHEME):
+            for key, bad in ((b.ARP_OPT_FINE_SCHEME, 3), (b.ARP_OPT_COARSE_SCHEME, 2)):
                 with pytest.raises(b.ArpError) as ei:
-                    b.arp_set_option(s.ctx, key, 2)
+                    b.arp_set_option(s.ctx, key, bad)
                 assert ei.value.status == b.ARP_EINVAL
             # batches take the default schemes only
             b.arp_set_initial(s.ctx, to_dev(x[0]))
@@ -163,3 +164,38 @@ def test_standard_parareal_finite_termination_on_gpu():
     for k, U in enumerate(its):
         for n in range(min(k, S) + 1):
             assert np.max(np.abs(U[n] - ser[n])) <= 1e-12 * scale, (k, n)
+
+
+# ----------------------------------------------------------- integrating-factor RK4
+
+@pytest.mark.parametrize("n,batch", [(8, 3), (64, 5), (256, 2), (512, 2), (2048, 1)])
+def test_ifrk4_fine_sweep_fp64_and_fp32(n, batch):
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    p = o.Params(n, 0.02, 1e-3 if n <= 256 else 1e-6, 0.02, 0.004, 8)
+    for prec, tol, amp in ((b.ARP_FP64, TOL64, 2.0), (b.ARP_FP32, TOL32, 0.5)):
+        x = _states(n, batch, 700 + n, float(n) * amp)
+        ref = o.ifrk4_propagate(x, p)
+        with _solver(b, p, batch, prec, fine=2) as s:
+            got = _call(b.arp_fine_batch, s, x)
+        assert per_state_rel_l2(got, ref).max() <= tol, prec
+
+
+def test_ifrk4_geostrophic_and_parareal():
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    from test_oracle_coarse import _geostrophic_state
+    p = o.Params(32, 0.01, 1e-3, 0.0625, 1e-3, 16)
+    u0 = _geostrophic_state(32, 4)[None]
+    decay = np.exp(-p.nu * np.arange(p.H) ** 4 * p.dT)
+    with _solver(b, p, 1, fine=2) as s:
+        np.testing.assert_allclose(_call(b.arp_fine_batch, s, u0)[0], decay * u0[0], atol=1e-13)
+    # the asymptotic method with the integrating-factor fine solver
+    w = ri.SMALL_N64
+    q = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+    v0 = w.initial_state()
+    ref = o.parareal(v0, q, w.slices, 2, F=lambda x: o.ifrk4_propagate(x, q))
+    for prec, tol in ((b.ARP_FP64, TOL64), (b.ARP_FP32, TOL32)):
+        its = _gpu_parareal(b, q, v0, w.slices, 2, prec, 2, 0)
+        for k in range(3):
+            assert per_state_rel_l2(its[k][1:], ref.iterates[k][1:]).max() <= tol, (prec, k)
