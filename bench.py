@@ -64,14 +64,15 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper"],
+    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper", "schemes"],
                     default="headline",
                     help="headline: the contract line (default); tts: time to 1e-5 relative error against the "
                          "serial fine solution (FP64 sweeps on the GPU), FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
                          "batched: 1024 uneven instances in one batch vs the FP64 path one instance at a time; "
                          "serve: Poisson request streams through the continuous-batching server; paper: the "
                          "experiments of Sec. 6.2 (Eq. 6.4 initial condition, eps = 1e-2, 1e-1, 1), asymptotic "
-                         "and standard parareal")
+                         "and standard parareal; schemes: the three fine solvers' sweep throughput and "
+                         "accuracy against the step size")
     ap.add_argument("--instances", type=int, default=1024)
     return ap.parse_args()
 
@@ -506,6 +507,76 @@ def run_paper(args) -> dict:
     return out
 
 
+def scheme_flops_per_grid_pt_step(scheme: int, n_grid: int) -> float:
+    """Algorithmic flops per grid-point-step of the fine schemes: ETDRK4 and
+    integrating-factor RK4 evaluate N four times per step (flops_per_grid_pt_step),
+    Strang splitting twice (2 x (17.5 log2 N + 52)) plus 20 for its combination."""
+    if scheme == 1:
+        return 35.0 * math.log2(n_grid) + 124.0
+    return flops_per_grid_pt_step(n_grid)
+
+
+def run_schemes(args) -> dict:
+    """The three fine solvers (ETDRK4, Strang splitting, integrating-factor RK4):
+    (1) one sweep of the large workload (256 slices, N = 512, 391 steps) per
+    scheme and precision, with algorithmic throughput against the ALU peak;
+    (2) accuracy at the step sizes Sec. 6.2 compares (dt = eps/10 .. eps/50 at
+    eps = 1e-2, N = 128, the Eq. 6.4 initial condition, one coarse step of the
+    experiment, dT = 0.5): max relative L-inf error against ETDRK4 at eps/400,
+    all in FP64 on the GPU."""
+    import numpy as np
+    import torch
+
+    import rsw_inputs as ri
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    w = WORKLOAD
+    names = {0: "etdrk4", 1: "strang", 2: "ifrk4"}
+    out = {"mode": "schemes", "workload": w.name, "sweep": {}, "accuracy": {}}
+    x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, w.slices, 9)).cuda()
+    y = torch.empty_like(x)
+    steps = fine_steps(w.dT, w.dt)
+    for prec, pname, peak in ((b.ARP_FP32, "fp32", FP32_ALU_PEAK_TFLOPS), (b.ARP_FP64, "fp64", FP64_ALU_PEAK_TFLOPS)):
+        for sch in (0, 1, 2):
+            with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
+                b.arp_set_option(s.ctx, b.ARP_OPT_FINE_SCHEME, sch)
+                b.arp_fine_batch(s.ctx, x, y)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(5 if prec == b.ARP_FP32 else 2):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    b.arp_fine_batch(s.ctx, x, y)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            units = w.slices * w.n_grid * steps
+            tf = units * scheme_flops_per_grid_pt_step(sch, w.n_grid) / (ms * 1e-3) / 1e12
+            out["sweep"][f"{names[sch]}_{pname}"] = {"ms": ms, "grid_pt_steps_per_s": units / (ms * 1e-3),
+                                                     "tflops": tf, "frac_of_alu_peak": tf / peak}
+    # accuracy against the step size
+    e = ri.PAPER_EXPERIMENTS[0]
+    n, dT = e.n_grid, e.dT
+    u0 = torch.from_numpy(ri.paper_initial_state(n)[None]).cuda()
+
+    def sweep(scheme, dt):
+        o_ = torch.empty_like(u0)
+        with b.Solver(n, e.eps, e.nu, 1, dT, dt, e.m_quad) as s:
+            b.arp_set_option(s.ctx, b.ARP_OPT_FINE_SCHEME, scheme)
+            b.arp_fine_batch(s.ctx, u0, o_)
+        return o_.cpu().numpy()
+
+    ref = sweep(0, e.eps / 400)
+    for sch in (0, 1, 2):
+        row = {}
+        for div in (10, 20, 25, 50):
+            row[f"eps/{div}"] = _linf_rel(sweep(sch, e.eps / div), ref, n)
+        out["accuracy"][names[sch]] = row
+    return out
+
+
 def run_precision(args) -> dict:
     """Precision sweep on the N=1024 instance (eps=1e-4, 512 slices, 1954 fine steps,
     M=128): per-field relative L2 error of one FP32-bulk fine sweep against the FP64
@@ -704,7 +775,7 @@ def main():
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             res = {"tts": run_tts, "precision": run_precision, "batched": run_batched, "serve": run_serve,
-                   "paper": run_paper}[args.mode](args)
+                   "paper": run_paper, "schemes": run_schemes}[args.mode](args)
             print(json.dumps(res), flush=True)
         return
     if args.impl == "reference":
