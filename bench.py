@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper", "schemes"],
+    ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper", "schemes",
+                                       "coarsegrid"],
                     default="headline",
                     help="headline: the contract line (default); tts: time to 1e-5 relative error against the "
                          "serial fine solution (FP64 sweeps on the GPU), FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
@@ -72,7 +73,7 @@ def parse():
                          "serve: Poisson request streams through the continuous-batching server; paper: the "
                          "experiments of Sec. 6.2 (Eq. 6.4 initial condition, eps = 1e-2, 1e-1, 1), asymptotic "
                          "and standard parareal; schemes: the three fine solvers' sweep throughput and "
-                         "accuracy against the step size")
+                         "accuracy against the step size; coarsegrid: the coarse solver on N/2 and N/4 points")
     ap.add_argument("--instances", type=int, default=1024)
     return ap.parse_args()
 
@@ -577,6 +578,50 @@ def run_schemes(args) -> dict:
     return out
 
 
+def run_coarsegrid(args) -> dict:
+    """The asymptotic coarse solver on a coarser spatial grid (ARP_OPT_COARSE_GRID)
+    at the large workload, FP32 bulk: for N_c = N, N/2, N/4, the time per parareal
+    iteration and of its chain, and the max relative L2 error of the iterates
+    k = 0..5 against the serial fine solution (FP64 sweeps chained on the GPU)."""
+    import numpy as np
+    import torch
+
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    w = WORKLOAD
+    H = w.n_grid // 2 + 1
+    u0 = torch.from_numpy(w.initial_state()).cuda()
+    ser = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
+    ser[0] = u0
+    with b.Solver(w.n_grid, w.eps, w.nu, 1, w.dT, w.dt, w.m_quad) as s:
+        for n in range(w.slices):
+            b.arp_fine_batch(s.ctx, ser[n:n + 1], ser[n + 1:n + 2])
+    ref = ser.cpu().numpy()
+    out = {"mode": "coarsegrid", "workload": w.name, "precision": "fp32", "runs": []}
+    U = torch.empty_like(ser)
+    for nc in (w.n_grid, w.n_grid // 2, w.n_grid // 4):
+        with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=b.ARP_FP32) as s:
+            b.arp_set_option(s.ctx, b.ARP_OPT_COARSE_GRID, nc)
+            errs, ms = [], []
+            for rep in range(2):  # the first pass warms up (and creates the coarse sub-context)
+                b.arp_set_initial(s.ctx, u0)
+                errs, ms = [], []
+                for k in range(6):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    b.arp_parareal_iterate(s.ctx)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                    b.arp_get_slices(s.ctx, U)
+                    x = U.cpu().numpy()
+                    errs.append(float(np.max(_parseval(x[1:] - ref[1:]) / _parseval(ref[1:]))))
+        out["runs"].append({"N_c": nc, "errors_per_k": errs, "predictor_ms": ms[0],
+                            "ms_per_iteration": statistics.median(ms[1:])})
+    return out
+
+
 def run_precision(args) -> dict:
     """Precision sweep on the N=1024 instance (eps=1e-4, 512 slices, 1954 fine steps,
     M=128): per-field relative L2 error of one FP32-bulk fine sweep against the FP64
@@ -775,7 +820,7 @@ def main():
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             res = {"tts": run_tts, "precision": run_precision, "batched": run_batched, "serve": run_serve,
-                   "paper": run_paper, "schemes": run_schemes}[args.mode](args)
+                   "paper": run_paper, "schemes": run_schemes, "coarsegrid": run_coarsegrid}[args.mode](args)
             print(json.dumps(res), flush=True)
         return
     if args.impl == "reference":

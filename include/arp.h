@@ -86,6 +86,15 @@ typedef enum {
                                  arp_coarse_step and the parareal chain.  arp_coarse_avg always
                                  computes the time average.  Batches (arp_batch_*) accept only
                                  the default schemes (ARP_EINVAL otherwise) */
+  ARP_OPT_COARSE_GRID = 10,  /* coarse solver on a coarser spatial grid (Sec. 1's remark on a
+                                coarser discretisation for the asymptotic solver): 0 (default) or
+                                N = the fine grid; a power of two N_c in [8, N) runs the coarse chain
+                                of the parareal iteration on the modes k <= (N_c - 1)/3 of an N_c
+                                grid, the higher modes of U following from F - G alone.  Applies to
+                                the asymptotic coarse scheme with the cluster chain
+                                (ARP_OPT_CHAIN 0); allocates a sub-context of
+                                arp_query_bytes(N_c, slices, M, precision) bytes on first use;
+                                arp_coarse_avg and arp_coarse_step keep the fine grid */
   ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook: a non-zero value makes
                                       block 0 of the next coarse-chain launch skip its first
                                       grid-barrier arrival, so every block's bounded wait

@@ -39,6 +39,8 @@ Functions and the passages they follow:
                        (the integrating factor method of Kassam & Trefethen)
   coarse_step_strang   one Strang step over dT: the coarse solver of standard
                        parareal on the full equation (Sec. 6.2)
+  restrict_state/prolong_state/coarse_step_on_grid   the asymptotic solver on a
+                       coarser grid (the remark on a coarser spatial discretisation, Sec. 1)
   parareal             the iteration of Eq. 3.1 (Algorithm 4)
   rel_change_norm      stopping quantity of Algorithm 4
   estimated_speedup    complexity model of Eq. 5.1
@@ -450,6 +452,25 @@ def coarse_step(u: np.ndarray, p: Params, nl: NonlinearFn = nonlinear) -> np.nda
     w = dhalf * w
     fast = 0.0 if math.isinf(p.eps) else dT / p.eps
     return _apply(expL(p, -fast), w)
+
+
+def restrict_state(u: np.ndarray, n_coarse: int) -> np.ndarray:
+    """The modes of u representable on n_coarse points, projected there (k <= K_c)."""
+    return project(np.array(u[..., : half_bins(n_coarse)], copy=True), n_coarse)
+
+
+def prolong_state(v: np.ndarray, n_grid: int) -> np.ndarray:
+    """A coarse-grid state on n_grid points: the missing modes are zero."""
+    out = np.zeros(v.shape[:-1] + (half_bins(n_grid),), dtype=np.complex128)
+    out[..., : v.shape[-1]] = v
+    return out
+
+
+def coarse_step_on_grid(u: np.ndarray, p: Params, n_coarse: int, nl: NonlinearFn = nonlinear) -> np.ndarray:
+    """The asymptotic slow solver (Algorithm 2) run on n_coarse points: restrict,
+    step with the same eps, nu, dT, window and nodes, prolong."""
+    pc = Params(n_coarse, p.eps, p.nu, p.dT, p.dt, p.m_quad, T0=p.T0, F=p.F)
+    return prolong_state(coarse_step(restrict_state(u, n_coarse), pc, nl), p.n_grid)
 
 
 # ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ ARP_OPT_CHAIN = 6
 ARP_OPT_FINE_BLOCK = 7
 ARP_OPT_FINE_SCHEME = 8
 ARP_OPT_COARSE_SCHEME = 9
+ARP_OPT_COARSE_GRID = 10
 ARP_OPT_TEST_SKIP_ARRIVAL = 100
 STATUS_NAMES = {0: "ARP_OK", 1: "ARP_EINVAL", 2: "ARP_ENOMEM", 3: "ARP_ECUDA", 4: "ARP_ETIMEOUT",
                 5: "ARP_ENONFINITE"}

@@ -25,6 +25,29 @@ arp_status ensure_tables(arp_ctx* c, cudaStream_t s) {
   return build_tables(c, s);
 }
 
+// The sub-context of ARP_OPT_COARSE_GRID: the same problem on N_c points (its
+// tables and chain buffers; its own slices' states are not used), kept in step
+// with the options that shape the coarse chain (window, F, precision).
+arp_status ensure_coarse(arp_ctx* c, cudaStream_t s) {
+  if (c->coarse_grid == 0) return ARP_OK;
+  if (!c->coarse) {
+    arp_ctx* q = nullptr;
+    const arp_status r = arp_create(&q, c->coarse_grid, c->eps, c->nu, c->slices, c->dT, c->dt, c->M);
+    if (r != ARP_OK) return fail(c, r, std::string("coarse grid: ") + arp_last_error(nullptr));
+    c->coarse = q;
+  }
+  arp_ctx* q = c->coarse;
+  if (q->T0_set != c->T0_set || q->T0 != c->T0 || q->F != c->F) {
+    q->T0 = c->T0;
+    q->T0_set = c->T0_set;
+    q->F = c->F;
+    q->tables_dirty = true;
+  }
+  q->precision = c->precision;
+  const arp_status r = ensure_tables(q, s);
+  return r == ARP_OK ? ARP_OK : fail(c, r, std::string("coarse grid: ") + q->err);
+}
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -258,6 +281,17 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       if (v != 0.0 && v != 1.0) return fail(c, ARP_EINVAL, "COARSE_SCHEME must be 0 (asymptotic) or 1 (Strang)");
       c->coarse_scheme = (int)v;
       return ARP_OK;
+    case ARP_OPT_COARSE_GRID: {
+      const int n = (int)v;
+      if ((double)n != v || (n != 0 && (n < 8 || n > c->N || (n & (n - 1)) != 0)))
+        return fail(c, ARP_EINVAL, "COARSE_GRID must be 0 or a power of two in [8, N]");
+      c->coarse_grid = (n == c->N) ? 0 : n;
+      if (c->coarse && c->coarse->N != c->coarse_grid) {
+        arp_destroy(c->coarse);
+        c->coarse = nullptr;
+      }
+      return ARP_OK;
+    }
     case ARP_OPT_FINE_BLOCK:
       if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1 or 2");
       c->fine_block = (int)v;
@@ -355,6 +389,7 @@ arp_status arp_get_slices(arp_ctx* c, double* U, void* stream) {
 
 arp_status arp_destroy(arp_ctx* c) {
   if (!c) return ARP_OK;
+  if (c->coarse) arp_destroy(c->coarse);
   release(c);
   delete c;
   return ARP_OK;

@@ -71,7 +71,7 @@ __global__ void corr_batch_kernel(const CorrJob* __restrict__ jobs, const int* _
 __global__ void finish_batch_kernel(const FinishJob* __restrict__ jobs, const int* __restrict__ first, int njobs) {
   const int i = find_job(first, njobs, blockIdx.x);
   const FinishJob j = jobs[i];
-  finish_body(j.Ge, j.V, j.U, j.Gc, blockIdx.x - first[i], j.H, j.K1, j.tb);
+  finish_body(j.Ge, j.V, j.U, j.Gc, blockIdx.x - first[i], j.H, j.K1, j.K1, j.tb);
 }
 
 // 256-thread blocks per (problem, slice n = 1..S): the relative change of the slice.
@@ -201,8 +201,8 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   arp_status r;
   std::vector<int> act, iter;  // indices: contexts with an initial state; those past their predictor
   for (int i = 0; i < n; ++i)
-    if (b->ctx[i]->fine_scheme != 0 || b->ctx[i]->coarse_scheme != 0)
-      return bfail(b, ARP_EINVAL, "batch: members must use the default fine and coarse schemes");
+    if (b->ctx[i]->fine_scheme != 0 || b->ctx[i]->coarse_scheme != 0 || b->ctx[i]->coarse_grid != 0)
+      return bfail(b, ARP_EINVAL, "batch: members must use the default fine and coarse schemes and grid");
   for (int i = 0; i < n; ++i) {
     arp_ctx* c = b->ctx[i];
     if (!c->have_initial) continue;
@@ -253,7 +253,7 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
         FineJob<double> j{c->Uold, c->Fb, c->steps, fine_tabs<double>(c)};
         memcpy(H + l.fine_off + (size_t)l.nfine * sizeof(j), &j, sizeof(j));
       }
-      CorrJob cj{c->Fb, c->Gc, c->V, c->VT, c->Uold, c->U, c->H, c->K1, basis_tabs(c)};
+      CorrJob cj{c->Fb, c->Gc, c->V, c->VT, c->Uold, c->U, c->H, c->K1, basis_tabs(c)};  // K1 = VT's modes
       memcpy(H + l.corr_off + (size_t)l.ncorr * sizeof(CorrJob), &cj, sizeof(cj));
       l.fine_blocks += c->slices;
       ++l.nfine;

@@ -63,6 +63,8 @@ struct arp_ctx {
   int fine_block = 0;            // ARP_OPT_FINE_BLOCK: 0 per-size default, 1 = N/4, 2 = N/2 threads
   int fine_scheme = 0;           // ARP_OPT_FINE_SCHEME: 0 ETDRK4, 1 Strang splitting, 2 integrating-factor RK4
   int coarse_scheme = 0;         // ARP_OPT_COARSE_SCHEME: 0 asymptotic (Algorithm 2), 1 Strang step of dT
+  int coarse_grid = 0;           // ARP_OPT_COARSE_GRID: 0 = the fine grid, else N_c < N for the coarse chain
+  arp_ctx* coarse = nullptr;     // owned sub-context on the N_c grid (its tables, chain buffers), made on first use
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;
 
@@ -114,5 +116,7 @@ arp_status launch_cluster_chain(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, 
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);
 // The serial chain of one context (cluster, else cooperative grid, else launches).
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s);
+// api.cu: the coarse-grid sub-context, created or refreshed to match c's options.
+arp_status ensure_coarse(arp_ctx* c, cudaStream_t s);
 
 }  // namespace arp

@@ -15,13 +15,13 @@
 namespace arp {
 
 __global__ void correction_kernel(const cd* __restrict__ F, const cd* __restrict__ G, cd* __restrict__ V,
-                                  cd* __restrict__ VT, int H, int K1, BasisTabs tb) {
-  corr_body(F, G, V, VT, blockIdx.x, H, K1, tb);
+                                  cd* __restrict__ VT, int H, int K1v, BasisTabs tb) {
+  corr_body(F, G, V, VT, blockIdx.x, H, K1v, tb);
 }
 
 __global__ void finish_kernel(const cd* __restrict__ Ge, const cd* __restrict__ V, cd* __restrict__ U,
-                              cd* __restrict__ Gc, int H, int K1, BasisTabs tb) {
-  finish_body(Ge, V, U, Gc, blockIdx.x, H, K1, tb);
+                              cd* __restrict__ Gc, int H, int K1, int K1g, BasisTabs tb) {
+  finish_body(Ge, V, U, Gc, blockIdx.x, H, K1, K1g, tb);
 }
 
 __global__ void slice_change_kernel(const cd* __restrict__ U, const cd* __restrict__ Uold, double* __restrict__ rel,
@@ -72,12 +72,26 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   // barrier counter and status word start at zero whichever kernel runs
   arp_status r = check_cuda(c, cudaMemsetAsync(c->sync, 0, 4 * sizeof(unsigned), s), "chain: status reset");
   if (r != ARP_OK) return r;
+  if (c->coarse_grid) {
+    // the asymptotic chain on the N_c grid (its sub-context's tables), from U_0
+    // restricted to the coarse modes; the finish prolongs g_n back onto N
+    if (c->coarse_scheme != 0 || c->chain_mode != 0 || c->skip_arrival)
+      return fail(c, ARP_EINVAL, "coarse grid: needs the asymptotic coarse scheme and the cluster chain");
+    arp_ctx* q = c->coarse;
+    if ((r = check_cuda(c, cudaMemcpy2DAsync(q->U, q->H * sizeof(cd), c->U, c->H * sizeof(cd), q->H * sizeof(cd), 3,
+                                             cudaMemcpyDeviceToDevice, s), "coarse grid: restrict u0")) != ARP_OK)
+      return r;
+    r = launch_cluster_chain(q, q->U, q->Ge, V ? q->VT : nullptr, s);
+    if (r != ARP_OK) return r == ARP_EINVAL ? fail(c, r, "coarse grid: no cluster chain fits") : fail(c, r, q->err);
+    finish_kernel<<<c->slices, 256, 0, s>>>(q->Ge, V, c->U, c->Gc, c->H, c->K1, q->K1, basis_tabs(c));
+    return check_cuda(c, cudaGetLastError(), "chain: finish");
+  }
   if (c->coarse_scheme == 1) return launch_strang_chain(c, c->U, c->Gc, V, s);
   r = ARP_EINVAL;
   if (c->chain_mode == 0 && !c->skip_arrival) {
     r = launch_cluster_chain(c, c->U, c->Ge, V ? c->VT : nullptr, s);
     if (r == ARP_OK) {
-      finish_kernel<<<c->slices, 256, 0, s>>>(c->Ge, V, c->U, c->Gc, c->H, c->K1, basis_tabs(c));
+      finish_kernel<<<c->slices, 256, 0, s>>>(c->Ge, V, c->U, c->Gc, c->H, c->K1, c->K1, basis_tabs(c));
       r = check_cuda(c, cudaGetLastError(), "chain: finish");
     }
   }
@@ -95,6 +109,7 @@ arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* cha
   const size_t st = (size_t)3 * c->H;  // complex entries per state
   const int S = c->slices;
   arp_status r;
+  if ((r = ensure_coarse(c, s)) != ARP_OK) return r;
   if (c->level < 0) {
     // predictor: U_{n+1} = G(U_n), G cached
     if ((r = run_chain(c, nullptr, s)) != ARP_OK) return r;
@@ -111,7 +126,11 @@ arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* cha
   }
   std::swap(c->U, c->Uold);
   if ((r = launch_fine(c, c->Uold, c->Fb, S, s)) != ARP_OK) return r;
-  correction_kernel<<<S, 256, 0, s>>>(c->Fb, c->Gc, c->V, c->VT, c->H, c->K1, basis_tabs(c));
+  {
+    cd* vt = c->coarse_grid ? c->coarse->VT : c->VT;
+    const int k1v = c->coarse_grid ? c->coarse->K1 : c->K1;
+    correction_kernel<<<S, 256, 0, s>>>(c->Fb, c->Gc, c->V, vt, c->H, k1v, basis_tabs(c));
+  }
   if ((r = check_cuda(c, cudaGetLastError(), "correction: launch")) != ARP_OK) return r;
   if ((r = check_cuda(c, cudaMemcpyAsync(c->U, c->Uold, st * sizeof(cd), cudaMemcpyDeviceToDevice, s),
                       "copy u0")) != ARP_OK)

@@ -19,10 +19,11 @@ struct BasisTabs {
 };
 
 // Slice n of the correction: V_n = F_n - G_n (all H bins, three fields) and,
-// for k < K1, VT_n = e^{dT/2 D} R^H V_n (three branches), the form in which
-// the cluster chain adds V_n to its eigen-basis state.
+// for k < K1v, VT_n = e^{dT/2 D} R^H V_n (three branches, row stride K1v), the
+// form in which the cluster chain adds V_n to its eigen-basis state (K1v < K1
+// when the chain runs on a coarser grid: only its modes are needed).
 __device__ __forceinline__ void corr_body(const cd* __restrict__ F, const cd* __restrict__ G, cd* __restrict__ V,
-                                          cd* __restrict__ VT, int n, int H, int K1, const BasisTabs& tb) {
+                                          cd* __restrict__ VT, int n, int H, int K1v, const BasisTabs& tb) {
   const size_t o = (size_t)n * 3 * H;
   for (int k = threadIdx.x; k < H; k += blockDim.x) {
     cd v[3];
@@ -31,27 +32,29 @@ __device__ __forceinline__ void corr_body(const cd* __restrict__ F, const cd* __
       v[f] = F[o + (size_t)f * H + k] - G[o + (size_t)f * H + k];
       V[o + (size_t)f * H + k] = v[f];
     }
-    if (k < K1) {
+    if (k < K1v) {
       cd e[3];
       phys_to_eigen<double>(v, tb.is64[k], tb.ss64[k], e);
 #pragma unroll
-      for (int b = 0; b < 3; ++b) VT[((size_t)n * 3 + b) * K1 + k] = tb.dhalf[k] * e[b];
+      for (int b = 0; b < 3; ++b) VT[((size_t)n * 3 + b) * K1v + k] = tb.dhalf[k] * e[b];
     }
   }
 }
 
 // Slice n after the cluster chain: the G cache G_n = R g_n (the imaginary
 // part of the k = 0 mode dropped, a real field's mean) and U_{n+1} = G_n + V_n
-// (V = null: the predictor), zero above the kept modes.
+// (V = null: the predictor), zero above the kept modes K1.  g_n has K1g modes
+// (row stride K1g); a chain on a coarser grid leaves G_n = 0 for K1g <= k < K1,
+// where U_{n+1} = V_n.
 __device__ __forceinline__ void finish_body(const cd* __restrict__ Ge, const cd* __restrict__ V, cd* __restrict__ U,
-                                            cd* __restrict__ Gc, int n, int H, int K1, const BasisTabs& tb) {
+                                            cd* __restrict__ Gc, int n, int H, int K1, int K1g, const BasisTabs& tb) {
   const size_t o = (size_t)n * 3 * H, o1 = (size_t)(n + 1) * 3 * H;
   for (int k = threadIdx.x; k < H; k += blockDim.x) {
     cd u[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
-    if (k < K1) {
+    if (k < K1g) {
       cd g[3];
 #pragma unroll
-      for (int b = 0; b < 3; ++b) g[b] = Ge[((size_t)n * 3 + b) * K1 + k];
+      for (int b = 0; b < 3; ++b) g[b] = Ge[((size_t)n * 3 + b) * K1g + k];
       eigen_to_phys<double>(g, tb.is64[k], tb.ss64[k], u);
       if (k == 0)
 #pragma unroll
@@ -67,10 +70,10 @@ __device__ __forceinline__ void finish_body(const cd* __restrict__ Ge, const cd*
 
 // One block per slice: corr_body.
 __global__ void correction_kernel(const cd* __restrict__ F, const cd* __restrict__ G, cd* __restrict__ V,
-                                  cd* __restrict__ VT, int H, int K1, BasisTabs tb);
+                                  cd* __restrict__ VT, int H, int K1v, BasisTabs tb);
 // One block per slice: finish_body.
 __global__ void finish_kernel(const cd* __restrict__ Ge, const cd* __restrict__ V, cd* __restrict__ U,
-                              cd* __restrict__ Gc, int H, int K1, BasisTabs tb);
+                              cd* __restrict__ Gc, int H, int K1, int K1g, BasisTabs tb);
 
 // ||U_n - Uold_n||^2 and ||U_n||^2 (Parseval weights 1 at k = 0, 2 above) of the
 // state at `base`, reduced by a 256-thread block in a fixed tree; thread 0

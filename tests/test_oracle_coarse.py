@@ -167,3 +167,32 @@ def test_nbar_approaches_resonant_average_with_long_windows():
         errs.append(o.parseval_norm(o.nbar(u, p) - exact))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.05 * o.parseval_norm(exact)
+
+
+def test_time_average_on_a_coarser_grid():
+    # For a state whose modes all fit the coarse grid's kept band, the 2/3 rule
+    # makes every product exact on both grids: the coarse-grid average equals the
+    # fine-grid average restricted to the coarse band (and G on the fine grid is
+    # G on a "coarse" grid of the same size).
+    n, nc = 64, 32
+    p = o.Params(n, 0.01, 1e-4, 0.0625, 1e-3, 16)
+    pc = o.Params(nc, 0.01, 1e-4, 0.0625, 1e-3, 16)
+    u = ri.random_spectrum(n, o.kept_modes(nc), 8.0, 11) * n
+    fine = o.nbar(u, p)
+    coarse = o.nbar(o.restrict_state(u, nc), pc)
+    np.testing.assert_allclose(coarse, o.restrict_state(fine, nc), atol=1e-13 * np.max(np.abs(fine)))
+    np.testing.assert_allclose(o.coarse_step_on_grid(u, p, n), o.coarse_step(u, p), atol=0)
+    g = o.coarse_step_on_grid(u, p, nc)
+    assert np.all(g[:, o.kept_modes(nc) + 1:] == 0)
+
+
+def test_parareal_with_coarse_grid_terminates_finitely():
+    n, nc, S = 32, 16, 4
+    p = o.Params(n, 0.05, 1e-4, 0.1, 0.01, 8)
+    u0 = ri.random_spectrum(n, 8, 16.0, 5) * 6.0
+    ser = o.serial_fine(u0, p, S)
+    res = o.parareal(u0, p, S, k_max=S, G=lambda x: o.coarse_step_on_grid(x, p, nc))
+    scale = np.max(np.abs(ser))
+    for k, U in enumerate(res.iterates):
+        for m in range(min(k, S) + 1):
+            assert np.max(np.abs(U[m] - ser[m])) < 1e-13 * scale, (k, m)
