@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper", "schemes",
-                                       "coarsegrid"],
+                                       "coarsegrid", "dftgemm"],
                     default="headline",
                     help="headline: the contract line (default); tts: time to 1e-5 relative error against the "
                          "serial fine solution (FP64 sweeps on the GPU), FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
@@ -73,7 +73,8 @@ def parse():
                          "serve: Poisson request streams through the continuous-batching server; paper: the "
                          "experiments of Sec. 6.2 (Eq. 6.4 initial condition, eps = 1e-2, 1e-1, 1), asymptotic "
                          "and standard parareal; schemes: the three fine solvers' sweep throughput and "
-                         "accuracy against the step size; coarsegrid: the coarse solver on N/2 and N/4 points")
+                         "accuracy against the step size; coarsegrid: the coarse solver on N/2 and N/4 points; "
+                         "dftgemm: the DFT-as-GEMM precisions against the FFT path")
     ap.add_argument("--instances", type=int, default=1024)
     return ap.parse_args()
 
@@ -622,12 +623,62 @@ def run_coarsegrid(args) -> dict:
     return out
 
 
+def run_dftgemm(args) -> dict:
+    """The DFT-as-GEMM precisions against the FFT path on the large workload:
+    one fine sweep of the 256 slices (391 ETDRK4 steps, all slices stepped
+    together in the GEMM precisions) and one batched time average of the 256
+    states over M = 64 nodes; wall time per call, algorithmic TFLOP/s counted
+    with FFT flops (so the dense 2 N (2K+1) flops per transform get no credit),
+    and the rate of the dense GEMM work itself."""
+    import torch
+
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    w = WORKLOAD
+    x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, w.slices, 9)).cuda()
+    y = torch.empty_like(x)
+    steps = fine_steps(w.dT, w.dt)
+    N, K = w.n_grid, (w.n_grid - 1) // 3
+    R = 2 * K + 1
+    out = {"mode": "dftgemm", "workload": w.name, "fine_sweep": {}, "time_average": {}}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for name, prec in (("fp32_fft", b.ARP_FP32), ("tf32x3_gemm", b.ARP_TF32X3), ("bf16x2_gemm", b.ARP_BF16X2)):
+        with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
+            ms = timed(lambda: b.arp_fine_batch(s.ctx, x, y), 3)
+            units = w.slices * N * steps
+            # dense work per step: 4 evaluations x (4 inverse + 3 forward columns) x 2 N R flops x 3 split products
+            dense = w.slices * steps * 4 * 7 * 2 * N * R * 3
+            out["fine_sweep"][name] = {"ms": ms, "algorithmic_tflops": units * flops_per_grid_pt_step(N) / ms / 1e9,
+                                       "dense_gemm_tflops": dense / ms / 1e9 if prec != b.ARP_FP32 else None}
+            ms = timed(lambda: b.arp_coarse_avg(s.ctx, x, y), 5)
+            nodes = w.slices * w.m_quad
+            fft_flops = nodes * N * (35.0 * math.log2(N) + 64.0)  # one N-evaluation per node
+            dense = nodes * 7 * 2 * N * R * 3
+            out["time_average"][name] = {"ms": ms, "algorithmic_tflops": fft_flops / ms / 1e9,
+                                         "dense_gemm_tflops": dense / ms / 1e9 if prec != b.ARP_FP32 else None}
+    return out
+
+
 def run_precision(args) -> dict:
     """Precision sweep on the N=1024 instance (eps=1e-4, 512 slices, 1954 fine steps,
-    M=128): per-field relative L2 error of one FP32-bulk fine sweep against the FP64
-    path (which the GPU tests hold to the FP64 oracle within 1e-10) and the mean-height
-    drift of both; then full-size parareal, FP32 against FP64 (iterates k = 0..3) and
-    the time per iteration of each."""
+    M=128): per-field relative L2 error of one fine sweep in FP32 bulk, 3xTF32 and
+    2xBF16 DFT-GEMMs against the FP64 path (which the GPU tests hold to the FP64
+    oracle within 1e-10) and the mean-height drift of each; then full-size parareal,
+    FP32 against FP64 (iterates k = 0..3) and the time per iteration of each."""
     import numpy as np
     import torch
 
@@ -641,7 +692,8 @@ def run_precision(args) -> dict:
     out = {"mode": "precision", "workload": w.name, "fine_sweep_vs_fp64": {}, "parareal_fp32_vs_fp64": {}}
     fields = ("v1", "v2", "h")
     iterates = {}
-    for name, prec in (("fp64", b.ARP_FP64), ("fp32", b.ARP_FP32)):
+    for name, prec in (("fp64", b.ARP_FP64), ("fp32", b.ARP_FP32), ("tf32x3", b.ARP_TF32X3),
+                       ("bf16x2", b.ARP_BF16X2)):
         with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
             xin = torch.from_numpy(x).cuda()
             y = torch.empty_like(xin)
@@ -653,6 +705,8 @@ def run_precision(args) -> dict:
                    for i, f in enumerate(fields)}
             drift = float(np.max(np.abs(got[:, 2, 0] - x[:, 2, 0].real) / np.abs(x[:, 2, 0].real)))
             out["fine_sweep_vs_fp64"][name] = {"rel_l2": rel, "mean_height_drift": drift}
+            if prec in (b.ARP_TF32X3, b.ARP_BF16X2):
+                continue  # the full-size parareal comparison below is FP32 against FP64
             b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
             U = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
             its, ms = [], []
@@ -820,7 +874,8 @@ def main():
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             res = {"tts": run_tts, "precision": run_precision, "batched": run_batched, "serve": run_serve,
-                   "paper": run_paper, "schemes": run_schemes, "coarsegrid": run_coarsegrid}[args.mode](args)
+                   "paper": run_paper, "schemes": run_schemes, "coarsegrid": run_coarsegrid,
+                   "dftgemm": run_dftgemm}[args.mode](args)
             print(json.dumps(res), flush=True)
         return
     if args.impl == "reference":

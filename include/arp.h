@@ -55,9 +55,17 @@ typedef enum {
 
 typedef enum {
   ARP_FP64 = 0,         /* all arithmetic in FP64 */
-  ARP_FP32 = 1          /* fine and coarse bulk arithmetic in FP32; tables and
+  ARP_FP32 = 1,         /* fine and coarse bulk arithmetic in FP32; tables and
                            phases computed in FP64 and rounded; parareal
                            correction and norm in FP64 */
+  ARP_TF32X3 = 2,       /* as ARP_FP32, but the real DFTs of the batched stages (the
+                           ETDRK4 fine sweep, all states stepped together, and the
+                           time average of arp_coarse_avg / arp_coarse_step) run as
+                           dense GEMMs on the tensor cores with TF32 operands split
+                           into high and low parts (three products, FP32
+                           accumulation); the serial coarse chain and the other fine
+                           schemes keep the FP32 FFT path */
+  ARP_BF16X2 = 3        /* as ARP_TF32X3 with BF16 high and low parts */
 } arp_precision;
 
 typedef enum {

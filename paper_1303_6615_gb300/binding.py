@@ -20,6 +20,7 @@ ARP_OK, ARP_EINVAL, ARP_ENOMEM, ARP_ECUDA, ARP_ETIMEOUT, ARP_ENONFINITE = range(
 ARP_FP64, ARP_FP32 = 0, 1
 ARP_OPT_T0, ARP_OPT_F, ARP_OPT_PRECISION, ARP_OPT_KMAX, ARP_OPT_TOL = 1, 2, 3, 4, 5
 ARP_OPT_CHAIN = 6
+ARP_TF32X3, ARP_BF16X2 = 2, 3
 ARP_OPT_FINE_BLOCK = 7
 ARP_OPT_FINE_SCHEME = 8
 ARP_OPT_COARSE_SCHEME = 9

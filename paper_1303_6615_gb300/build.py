@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libarp.so")
 
 SOURCES = ["api.cu", "tables.cu", "fine64.cu", "fine32.cu", "chain64.cu", "chain32.cu", "coarse.cu", "strang64.cu",
-           "strang32.cu", "ifrk64.cu", "ifrk32.cu",
+           "strang32.cu", "ifrk64.cu", "ifrk32.cu", "dftgemm.cu",
            "parareal.cu", "static_avg.cu",
            "batch.cu", "batch64.cu", "batch32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -72,7 +72,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags: list[str] | N
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

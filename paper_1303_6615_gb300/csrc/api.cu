@@ -65,11 +65,11 @@ struct Sizes {
 };
 
 // States per pass of the batched time average: all slices, but at most what a
-// 8 MiB partial-sum workspace holds (at least one); the parareal path does
+// 32 MiB partial-sum workspace holds (at least one); the parareal path does
 // not use this workspace.
 int coarse_chunk(int slices, size_t P, size_t K1) {
   const size_t per = P * 3 * K1 * 16;
-  size_t c = ((size_t)8 << 20) / per;
+  size_t c = ((size_t)32 << 20) / per;
   if (c < 1) c = 1;
   return (int)(c < (size_t)slices ? c : (size_t)slices);
 }
@@ -101,6 +101,7 @@ arp_status alloc(arp_ctx* c, P** p, size_t bytes) {
 }
 
 void release(arp_ctx* c) {
+  dft_release(c);
   void* ptrs[] = {c->E_lo32, c->inv_sig64, c->sk_sig64, c->inv_sig32, c->sk_sig32, c->etd64,   c->etd32, c->tw64,
                   c->tw32,      c->phase64,  c->phase32,   c->weight64,  c->weight32, c->dhalf, c->gphase,
                   c->W,         c->W2,       c->partial,   c->rel,       c->scalar,   c->U,     c->Uold,
@@ -179,7 +180,7 @@ using namespace arp;
 extern "C" {
 
 size_t arp_query_bytes(int N, int slices, int M, int precision) {
-  if (!pow2_in_range(N) || slices < 1 || M < 2 || (precision != ARP_FP64 && precision != ARP_FP32)) return 0;
+  if (!pow2_in_range(N) || slices < 1 || M < 2 || precision < ARP_FP64 || precision > ARP_BF16X2) return 0;
   Sizes z = sizes_of(N, slices, M);
   return z.tables + z.work + z.state;
 }
@@ -257,7 +258,8 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       c->tables_dirty = true;
       return ARP_OK;
     case ARP_OPT_PRECISION:
-      if (v != (double)ARP_FP64 && v != (double)ARP_FP32) return fail(c, ARP_EINVAL, "unknown precision");
+      if (v != (double)ARP_FP64 && v != (double)ARP_FP32 && v != (double)ARP_TF32X3 && v != (double)ARP_BF16X2)
+        return fail(c, ARP_EINVAL, "unknown precision");
       c->precision = (int)v;
       return ARP_OK;
     case ARP_OPT_KMAX:

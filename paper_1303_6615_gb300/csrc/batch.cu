@@ -201,8 +201,9 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   arp_status r;
   std::vector<int> act, iter;  // indices: contexts with an initial state; those past their predictor
   for (int i = 0; i < n; ++i)
-    if (b->ctx[i]->fine_scheme != 0 || b->ctx[i]->coarse_scheme != 0 || b->ctx[i]->coarse_grid != 0)
-      return bfail(b, ARP_EINVAL, "batch: members must use the default fine and coarse schemes and grid");
+    if (b->ctx[i]->fine_scheme != 0 || b->ctx[i]->coarse_scheme != 0 || b->ctx[i]->coarse_grid != 0 ||
+        dft_mode(b->ctx[i]))
+      return bfail(b, ARP_EINVAL, "batch: members must use the default schemes and grid, FP64 or FP32");
   for (int i = 0; i < n; ++i) {
     arp_ctx* c = b->ctx[i];
     if (!c->have_initial) continue;

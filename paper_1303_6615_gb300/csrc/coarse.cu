@@ -61,6 +61,8 @@ __global__ void reduce_kernel(ReduceArgs r) {
   }
   cd nb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
   const cd* src = r.partial + (size_t)b * r.P * 3 * r.K1;
+  // chunk order; unrolled so that the loads of several chunks are in flight at once
+#pragma unroll 8
   for (int p = 0; p < r.P; ++p)
     for (int q = 0; q < 3; ++q) nb[q] = nb[q] + src[((size_t)p * 3 + q) * r.K1 + k];
   const cd* w = r.W ? r.W + (size_t)b * 3 * r.K1 : nullptr;
@@ -100,7 +102,8 @@ arp_status launch_nbar_reduce(arp_ctx* c, int mode, const cd* partial, const cd*
                               const cd* vadd, cd* out2_phys, int batch, cudaStream_t s) {
   const long long n = (long long)batch * c->H;
   if (n == 0) return ARP_OK;
-  ReduceArgs r{mode, batch, c->H, c->K1, c->P, c->dT, partial, W, W2, out_phys, vadd, out2_phys,
+  // the DFT-GEMM time average writes the whole node sum as one chunk
+  ReduceArgs r{mode, batch, c->H, c->K1, dft_mode(c) ? 1 : c->P, c->dT, partial, W, W2, out_phys, vadd, out2_phys,
                c->inv_sig64, c->sk_sig64, c->dhalf, c->gphase};
   reduce_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(r);
   return check_cuda(c, cudaGetLastError(), "reduce: launch");

@@ -9,6 +9,10 @@
 #include "arp.h"
 #include "common.cuh"
 
+namespace arp {
+struct DftWork;  // dftgemm.cu: DFT matrices, GEMM operands, cuBLAS handle
+}
+
 struct arp_ctx {
   // problem
   int N = 0, logN = 0, H = 0, K = 0, K1 = 0;
@@ -65,6 +69,7 @@ struct arp_ctx {
   int coarse_scheme = 0;         // ARP_OPT_COARSE_SCHEME: 0 asymptotic (Algorithm 2), 1 Strang step of dT
   int coarse_grid = 0;           // ARP_OPT_COARSE_GRID: 0 = the fine grid, else N_c < N for the coarse chain
   arp_ctx* coarse = nullptr;     // owned sub-context on the N_c grid (its tables, chain buffers), made on first use
+  arp::DftWork* dft = nullptr;   // ARP_TF32X3 / ARP_BF16X2 workspace, made on first use
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;
 
@@ -118,5 +123,12 @@ arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* cha
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s);
 // api.cu: the coarse-grid sub-context, created or refreshed to match c's options.
 arp_status ensure_coarse(arp_ctx* c, cudaStream_t s);
+// dftgemm.cu: the DFT-as-GEMM precisions (ARP_TF32X3, ARP_BF16X2): the time
+// average's node terms as one chunk partial [batch][1][3][K1], and the ETDRK4
+// fine sweep with all states stepped together.
+bool dft_mode(const arp_ctx* c);
+arp_status dft_nbar(arp_ctx* c, const cd* W, cd* partial, int batch, cudaStream_t s);
+arp_status dft_fine(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s);
+void dft_release(arp_ctx* c);
 
 }  // namespace arp
