@@ -76,6 +76,8 @@ def parse():
                          "accuracy against the step size; coarsegrid: the coarse solver on N/2 and N/4 points; "
                          "dftgemm: the DFT-as-GEMM precisions against the FFT path")
     ap.add_argument("--instances", type=int, default=1024)
+    ap.add_argument("--probe", action="store_true",
+                    help="with --mode dftgemm: only one small time average (a case sized for a profiler)")
     return ap.parse_args()
 
 
@@ -636,6 +638,15 @@ def run_dftgemm(args) -> dict:
     from paper_1303_6615_gb300 import build as bld
     bld.build()
     w = WORKLOAD
+    if args.probe:
+        # one time average in ARP_TF32X3 on 16 states, twice: a small case for a profiler
+        x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, 16, 9)).cuda()
+        y = torch.empty_like(x)
+        with b.Solver(w.n_grid, w.eps, w.nu, 16, w.dT, w.dt, w.m_quad, precision=b.ARP_TF32X3) as s:
+            for _ in range(2):
+                b.arp_coarse_avg(s.ctx, x, y)
+        torch.cuda.synchronize()
+        return {"mode": "dftgemm", "probe": "one ARP_TF32X3 time average of 16 states, twice"}
     x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, w.slices, 9)).cuda()
     y = torch.empty_like(x)
     steps = fine_steps(w.dT, w.dt)
