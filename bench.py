@@ -141,6 +141,25 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- our arm
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (every rank gets it); the job's time is its
+    slowest rank's.  Works with any initialised backend (NCCL with a CUDA device,
+    gloo on the CPU)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job units per second: every rank's replica does units_per_step per
+    step, over the slowest rank's time."""
+    return units_per_step * steps * world / (max_ms / 1e3)
+
+
 def run_ours(args, rank: int, world: int) -> dict | None:
     import torch
     import torch.distributed as dist
@@ -189,12 +208,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(z) for a, z in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = units * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, "cuda")
+    value = job_throughput(units, args.steps, world, total_ms)
 
     # dominant kernel: the fine sweep over all slices, timed live with events on its stream
     U = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
