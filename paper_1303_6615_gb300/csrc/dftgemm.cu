@@ -213,33 +213,17 @@ __global__ void dft_fine_stage_kernel(const float* __restrict__ Q, int S_, int K
   const int k = (int)(t % K1), s = (int)(t / K1);
   cf bn[3];
   unpack_columns(Q, k, K, R, tb.is[k], tb.ss[k], (size_t)s, bn);
-  const EtdView<float> e = tb.etd;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const int i = q * K1 + k;
     const size_t o = ((size_t)s * 3 + q) * K1 + k;
-    if (stage == 0) {
-      NU[o] = bn[q];
-      const cf a = ldgc(e.E2 + i) * U[o] + ldgc(e.Q + i) * bn[q];
-      A1[o] = a;
-      const cdf sum = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(tb.E_lo + i), U[o], ULO[o]), ldgc(e.f1 + i) * bn[q]);
-      ACC[o] = mk<float>(sum.re.hi, sum.im.hi);
-      ACCLO[o] = mk<float>(sum.re.lo, sum.im.lo);
-      XS[o] = a;
-    } else if (stage == 3) {
-      const cf tt = ldgc(e.f3 + i) * bn[q];
-      const df re = df_add_f(df{ACC[o].x, ACCLO[o].x}, tt.x), im = df_add_f(df{ACC[o].y, ACCLO[o].y}, tt.y);
-      U[o] = mk<float>(re.hi, im.hi);
-      ULO[o] = mk<float>(re.lo, im.lo);
-      XS[o] = U[o];
-    } else {
-      const cf tt = ldgc(e.f2x2 + i) * bn[q];
-      const df re = df_add_f(df{ACC[o].x, ACCLO[o].x}, tt.x), im = df_add_f(df{ACC[o].y, ACCLO[o].y}, tt.y);
-      ACC[o] = mk<float>(re.hi, im.hi);
-      ACCLO[o] = mk<float>(re.lo, im.lo);
-      XS[o] = (stage == 1) ? ldgc(e.E2 + i) * U[o] + ldgc(e.Q + i) * bn[q]
-                           : ldgc(e.E2 + i) * A1[o] + ldgc(e.Q + i) * (2.0f * bn[q] - NU[o]);
-    }
+    cf u = U[o], ulo = ULO[o], nu = NU[o], a1 = A1[o], acc = ACC[o], acclo = ACCLO[o];
+    XS[o] = etd32_stage(stage, q * K1 + k, bn[q], u, ulo, nu, a1, acc, acclo, tb.etd, tb.E_lo);
+    U[o] = u;
+    ULO[o] = ulo;
+    NU[o] = nu;
+    A1[o] = a1;
+    ACC[o] = acc;
+    ACCLO[o] = acclo;
   }
 }
 

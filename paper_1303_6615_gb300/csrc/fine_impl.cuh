@@ -283,6 +283,38 @@ struct F32Layout {
   static constexpr size_t kBytes = (size_t)lanes_and_twiddles<float>(LOGN) * sizeof(cf) + (size_t)2 * K1 * sizeof(float);
 };
 
+// One ETDRK4 stage of the FP32 path for one (wavenumber, branch) entry i of the
+// tables: given N of the stage's input (bn), update (in place) the float-pair
+// state u/ulo, N(u), a1 and the float-pair update sum acc/acclo, and return the
+// next stage's input.  Shared by the register-resident sweep and the lock-step
+// DFT-GEMM sweep so both apply the same arithmetic.
+__device__ __forceinline__ cf etd32_stage(int stage, int i, cf bn, cf& u, cf& ulo, cf& nu, cf& a1, cf& acc,
+                                          cf& acclo, const EtdView<float>& e, const cf* __restrict__ E_lo) {
+  if (stage == 0) {
+    nu = bn;
+    a1 = ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn;
+    const cdf s = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(E_lo + i), u, ulo), ldgc(e.f1 + i) * bn);
+    acc = mk<float>(s.re.hi, s.im.hi);
+    acclo = mk<float>(s.re.lo, s.im.lo);
+    return a1;
+  } else if (stage == 3) {
+    const cf t = ldgc(e.f3 + i) * bn;
+    const df re = df_add_f(df{acc.x, acclo.x}, t.x);
+    const df im = df_add_f(df{acc.y, acclo.y}, t.y);
+    u = mk<float>(re.hi, im.hi);
+    ulo = mk<float>(re.lo, im.lo);
+    return u;
+  } else {
+    const cf t = ldgc(e.f2x2 + i) * bn;
+    const df re = df_add_f(df{acc.x, acclo.x}, t.x);
+    const df im = df_add_f(df{acc.y, acclo.y}, t.y);
+    acc = mk<float>(re.hi, im.hi);
+    acclo = mk<float>(re.lo, im.lo);
+    return (stage == 1) ? ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn
+                        : ldgc(e.E2 + i) * a1 + ldgc(e.Q + i) * (2.0f * bn - nu);
+  }
+}
+
 template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
 __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
                                               const FineTabs<float>& tb, int slice) {
@@ -365,28 +397,9 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
               acclo[r][q] = mk<float>(re.lo, im.lo);
               nx[q] = (stage == 1) ? E2 * u[r][q] + (0.5f * h) * bn[q] : ldgc(e.E + i) * u[r][q] + h * w;
             }
-          } else if (stage == 0) {
-            nu[r][q] = bn[q];
-            a1[r][q] = ldgc(e.E2 + i) * u[r][q] + ldgc(e.Q + i) * bn[q];
-            const cdf s = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(tb.E_lo + i), u[r][q], ulo[r][q]), ldgc(e.f1 + i) * bn[q]);
-            acc[r][q] = mk<float>(s.re.hi, s.im.hi);
-            acclo[r][q] = mk<float>(s.re.lo, s.im.lo);
-            nx[q] = a1[r][q];
-          } else if (stage == 3) {
-            const cf t = ldgc(e.f3 + i) * bn[q];
-            const df re = df_add_f(df{acc[r][q].x, acclo[r][q].x}, t.x);
-            const df im = df_add_f(df{acc[r][q].y, acclo[r][q].y}, t.y);
-            u[r][q] = mk<float>(re.hi, im.hi);
-            ulo[r][q] = mk<float>(re.lo, im.lo);
-            nx[q] = u[r][q];
           } else {
-            const cf t = ldgc(e.f2x2 + i) * bn[q];
-            const df re = df_add_f(df{acc[r][q].x, acclo[r][q].x}, t.x);
-            const df im = df_add_f(df{acc[r][q].y, acclo[r][q].y}, t.y);
-            acc[r][q] = mk<float>(re.hi, im.hi);
-            acclo[r][q] = mk<float>(re.lo, im.lo);
-            nx[q] = (stage == 1) ? ldgc(e.E2 + i) * u[r][q] + ldgc(e.Q + i) * bn[q]
-                                 : ldgc(e.E2 + i) * a1[r][q] + ldgc(e.Q + i) * ((T)2 * bn[q] - nu[r][q]);
+            nx[q] = etd32_stage(stage, i, bn[q], u[r][q], ulo[r][q], nu[r][q], a1[r][q], acc[r][q], acclo[r][q], e,
+                                tb.E_lo);
           }
         }
         if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
