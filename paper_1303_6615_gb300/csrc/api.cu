@@ -271,7 +271,7 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       c->tol = v;
       return ARP_OK;
     case ARP_OPT_CHAIN:
-      if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "CHAIN must be 0, 1 or 2");
+      if (v != 0.0 && v != 1.0 && v != 2.0 && v != 3.0) return fail(c, ARP_EINVAL, "CHAIN must be 0, 1, 2 or 3");
       c->chain_mode = (int)v;
       return ARP_OK;
     case ARP_OPT_FINE_SCHEME:

@@ -275,7 +275,13 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
     std::vector<ClusterPlan> plans(g.second.size());
     arp_status pr = ARP_EINVAL;
     bool forced = false;
-    for (int i : g.second) forced |= (b->ctx[i]->chain_mode != 0 || b->ctx[i]->skip_arrival);
+    // a member whose chain would not run as a cluster on its own runs it on its own here too
+    // (FP64 in automatic mode prefers the cooperative grid), so batched = solo bit for bit
+    for (int i : g.second) {
+      const arp_ctx* c = b->ctx[i];
+      forced |= (c->chain_mode == 1 || c->chain_mode == 2 || c->skip_arrival ||
+                 (c->chain_mode == 0 && c->precision == ARP_FP64));
+    }
     if (!forced)
       pr = f32 ? plan_chain_batch_f32(l.logN, M.data(), K1.data(), (int)M.size(), &l.C, plans.data(), &l.smem)
                : plan_chain_batch_f64(l.logN, M.data(), K1.data(), (int)M.size(), &l.C, plans.data(), &l.smem);

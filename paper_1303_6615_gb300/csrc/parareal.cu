@@ -63,9 +63,10 @@ arp_status chain_status(arp_ctx* c, unsigned status) {
 
 // The whole serial chain n = 0..S-1: one thread-block cluster (then the
 // parallel finish: U and the G cache from the eigen-basis g_n), else the
-// persistent cooperative kernel, else one link at a time (ARP_OPT_CHAIN
-// restricts the choice; the barrier-timeout test hook needs the cooperative
-// kernel, whose grid barriers are the bounded waits it exercises).  V, if not
+// persistent cooperative kernel, else one link at a time; in FP64 the
+// cooperative kernel is tried first (ARP_OPT_CHAIN restricts the choice; the
+// barrier-timeout test hook needs the cooperative kernel, whose grid barriers
+// are the bounded waits it exercises).  V, if not
 // null, is c->V, whose eigen form c->VT the correction kernel wrote with it.
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   const size_t st = (size_t)3 * c->H;
@@ -75,7 +76,7 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   if (c->coarse_grid) {
     // the asymptotic chain on the N_c grid (its sub-context's tables), from U_0
     // restricted to the coarse modes; the finish prolongs g_n back onto N
-    if (c->coarse_scheme != 0 || c->chain_mode != 0 || c->skip_arrival)
+    if (c->coarse_scheme != 0 || (c->chain_mode != 0 && c->chain_mode != 3) || c->skip_arrival)
       return fail(c, ARP_EINVAL, "coarse grid: needs the asymptotic coarse scheme and the cluster chain");
     arp_ctx* q = c->coarse;
     if ((r = check_cuda(c, cudaMemcpy2DAsync(q->U, q->H * sizeof(cd), c->U, c->H * sizeof(cd), q->H * sizeof(cd), 3,
@@ -88,7 +89,11 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   }
   if (c->coarse_scheme == 1) return launch_strang_chain(c, c->U, c->Gc, V, s);
   r = ARP_EINVAL;
-  if (c->chain_mode == 0 && !c->skip_arrival) {
+  // In FP64 the chain's transforms are bound by GB300's FP64 throughput, so the
+  // cooperative grid (up to one node per SM) comes first; otherwise the cluster.
+  if (c->chain_mode == 0 && c->precision == ARP_FP64 && !c->skip_arrival) r = launch_chain(c, c->U, c->Gc, V, s);
+  if (r != ARP_EINVAL) return r;
+  if ((c->chain_mode == 0 || c->chain_mode == 3) && !c->skip_arrival) {
     r = launch_cluster_chain(c, c->U, c->Ge, V ? c->VT : nullptr, s);
     if (r == ARP_OK) {
       finish_kernel<<<c->slices, 256, 0, s>>>(c->Ge, V, c->U, c->Gc, c->H, c->K1, c->K1, basis_tabs(c));
@@ -96,6 +101,7 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
     }
   }
   if (r != ARP_EINVAL) return r;
+  if (c->chain_mode == 3) return fail(c, ARP_EINVAL, "chain: no cluster chain fits (ARP_OPT_CHAIN 3)");
   if (c->chain_mode <= 1) r = launch_chain(c, c->U, c->Gc, V, s);
   if (r != ARP_EINVAL) return r;
   for (int n = 0; n < c->slices; ++n)

@@ -172,7 +172,7 @@ def _gpu_parareal(p, u0, slices, iters, precision=0, chain=0):
     return its, changes
 
 
-@pytest.mark.parametrize("chain", [0, 1, 2], ids=["cluster", "cooperative", "launches"])
+@pytest.mark.parametrize("chain", [0, 1, 2, 3], ids=["auto", "cooperative", "launches", "cluster"])
 def test_parareal_small_workload_fp64(chain):
     w = ri.SMALL_N64
     p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
@@ -289,7 +289,7 @@ def test_coarse_fp32():
     assert per_state_rel_l2(g, o.coarse_step(x, p)).max() <= TOL32
 
 
-@pytest.mark.parametrize("chain", [0, 1], ids=["cluster", "cooperative"])
+@pytest.mark.parametrize("chain", [0, 1, 3], ids=["auto", "cooperative", "cluster"])
 def test_parareal_small_workload_fp32(chain):
     from paper_1303_6615_gb300 import binding as b
     w = ri.SMALL_N64
