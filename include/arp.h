@@ -104,6 +104,18 @@ typedef enum {
                                 (ARP_OPT_CHAIN 0); allocates a sub-context of
                                 arp_query_bytes(N_c, slices, M, precision) bytes on first use;
                                 arp_coarse_avg and arp_coarse_step keep the fine grid */
+  ARP_OPT_PIPELINE = 11,  /* arp_parareal_solve as a pipeline across iterations: 0 = off (one
+                             level after another), 1 = on with chunks of max(4, ceil(S/16))
+                             links (default), n >= 2 = chunks of n links.  The SMs are split
+                             into two partitions (green contexts): one that holds the coarse
+                             chain's thread-block cluster, one for the fine sweeps, which start
+                             on a chunk's slices as soon as the chain has produced their start
+                             states.  Results, level and change equal the level-by-level solve's
+                             bit for bit.  Applies with the cluster chain (FP32 with ARP_OPT_CHAIN
+                             0, or ARP_OPT_CHAIN 3), the asymptotic coarse scheme on the fine
+                             grid and the FFT precisions; elsewhere, or where the partition
+                             cannot be made, the solve runs level by level.  Allocates one
+                             more [slices][3][H] FP64 buffer on first use */
   ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook: a non-zero value makes
                                       block 0 of the next coarse-chain launch skip its first
                                       grid-barrier arrival, so every block's bounded wait
@@ -194,7 +206,15 @@ arp_status arp_parareal_iterate(arp_ctx* ctx, void* stream, int* k_done,
                                 double* max_rel_change);
 
 /* arp_parareal_solve: arp_parareal_iterate until k = KMAX or the change is
- * <= TOL (options), starting from the current level. */
+ * <= TOL (options), starting from the current level.  With ARP_OPT_PIPELINE
+ * (default on, where it applies) the levels overlap on the device: the fine
+ * sweep of level k starts on a chunk of slices as soon as the chain of level
+ * k has produced their start states, on SMs the chain does not use; the
+ * result, level and change are the level-by-level solve's, bit for bit.  When
+ * the tolerance stops the solve at level k, the fine sweep of level k started
+ * speculatively still completes before the work that follows on `stream`.
+ * Returns after the last level's change is read; the slices are ready in
+ * `stream` order.  ARP_EINVAL if no initial state was set. */
 arp_status arp_parareal_solve(arp_ctx* ctx, void* stream, int* k_done, double* max_rel_change);
 
 /* arp_get_slices: copy the current iterate U_0..U_S, [(S+1)][3][H] complex
@@ -266,6 +286,12 @@ const char* arp_batch_last_error(const arp_batch* batch);
  * out[4]=M, out[5]=fine steps per slice, out[6]=current level k (-1 before the
  * predictor), out[7]=precision. */
 arp_status arp_info(const arp_ctx* ctx, int* out8);
+
+/* arp_pipeline_info: how the last arp_parareal_solve ran: out[0] = 1 if
+ * pipelined (ARP_OPT_PIPELINE), else 0; out[1], out[2] = SMs of the chain and
+ * fine partitions, out[3] = links per chunk, out[4] = CTAs of the chain's
+ * cluster (0 where no partition was made).  ARP_EINVAL for NULL arguments. */
+arp_status arp_pipeline_info(const arp_ctx* ctx, int* out5);
 
 #ifdef __cplusplus
 }

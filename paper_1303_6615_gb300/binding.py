@@ -25,6 +25,7 @@ ARP_OPT_FINE_BLOCK = 7
 ARP_OPT_FINE_SCHEME = 8
 ARP_OPT_COARSE_SCHEME = 9
 ARP_OPT_COARSE_GRID = 10
+ARP_OPT_PIPELINE = 11
 ARP_OPT_TEST_SKIP_ARRIVAL = 100
 STATUS_NAMES = {0: "ARP_OK", 1: "ARP_EINVAL", 2: "ARP_ENOMEM", 3: "ARP_ECUDA", 4: "ARP_ETIMEOUT",
                 5: "ARP_ENONFINITE"}
@@ -48,6 +49,7 @@ _SIGS = {
     "arp_destroy": (ctypes.c_int, [_P]),
     "arp_last_error": (ctypes.c_char_p, [_P]),
     "arp_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "arp_pipeline_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "arp_coarse_avg_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P,
                                              _P, ctypes.c_int, _P]),
     "arp_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
@@ -125,6 +127,13 @@ def arp_info(ctx: int) -> dict:
     out = (ctypes.c_int * 8)()
     _check(ctx, load_library().arp_info(ctx, out))
     keys = ("N", "H", "K", "slices", "M", "steps", "level", "precision")
+    return dict(zip(keys, list(out)))
+
+
+def arp_pipeline_info(ctx: int) -> dict:
+    out = (ctypes.c_int * 5)()
+    _check(ctx, load_library().arp_pipeline_info(ctx, out))
+    keys = ("pipelined", "chain_sms", "fine_sms", "chunk", "cluster")
     return dict(zip(keys, list(out)))
 
 

@@ -101,6 +101,7 @@ arp_status alloc(arp_ctx* c, P** p, size_t bytes) {
 }
 
 void release(arp_ctx* c) {
+  pipeline_release(c);
   dft_release(c);
   void* ptrs[] = {c->E_lo32, c->inv_sig64, c->sk_sig64, c->inv_sig32, c->sk_sig32, c->etd64,   c->etd32, c->tw64,
                   c->tw32,      c->phase64,  c->phase32,   c->weight64,  c->weight32, c->dhalf, c->gphase,
@@ -294,6 +295,11 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       }
       return ARP_OK;
     }
+    case ARP_OPT_PIPELINE:
+      if (!(v >= 0.0) || v > 1e9 || v != std::floor(v))
+        return fail(c, ARP_EINVAL, "PIPELINE must be 0, 1 or a chunk length >= 2");
+      c->pipeline = (int)v;
+      return ARP_OK;
     case ARP_OPT_FINE_BLOCK:
       if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1 or 2");
       c->fine_block = (int)v;
@@ -369,9 +375,18 @@ arp_status arp_parareal_iterate(arp_ctx* c, void* stream, int* k_done, double* c
 
 arp_status arp_parareal_solve(arp_ctx* c, void* stream, int* k_done, double* change) {
   if (!c) return ARP_EINVAL;
+  if (!c->have_initial) return fail(c, ARP_EINVAL, "no initial state: call arp_set_initial first");
+  cudaStream_t s = (cudaStream_t)stream;
+  arp_status r = ensure_tables(c, s);
+  if (r != ARP_OK) return r;
+  c->last_pipelined = 0;
+  if (pipeline_eligible(c) && c->level < c->kmax) {
+    bool ran = false;
+    r = parareal_solve_pipelined(c, s, &ran, k_done, change);
+    if (ran || r != ARP_OK) return r;
+  }
   int k = c->level;
   double ch = INFINITY;
-  arp_status r = ARP_OK;
   while (r == ARP_OK && k < c->kmax && !(k >= 1 && ch <= c->tol)) r = arp_parareal_iterate(c, stream, &k, &ch);
   if (k_done) *k_done = k;
   if (change) *change = ch;
@@ -395,6 +410,11 @@ arp_status arp_destroy(arp_ctx* c) {
   release(c);
   delete c;
   return ARP_OK;
+}
+
+arp_status arp_pipeline_info(const arp_ctx* c, int* out5) {
+  if (!c || !out5) return ARP_EINVAL;
+  return pipeline_info(c, out5);
 }
 
 const char* arp_last_error(const arp_ctx* c) {

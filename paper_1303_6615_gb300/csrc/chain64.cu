@@ -6,11 +6,13 @@
 namespace arp {
 
 arp_status launch_chain_f32(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
-arp_status launch_cluster_chain_f32(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s);
+arp_status launch_cluster_chain_f32(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s,
+                                    const ChainRange* rg);
 
-arp_status launch_cluster_chain(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s) {
-  if (c->precision != ARP_FP64) return launch_cluster_chain_f32(c, U0, Ge, VT, s);
-  return launch_cluster_chain_prec<double>(c, U0, Ge, VT, s);
+arp_status launch_cluster_chain(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s,
+                                const ChainRange* rg) {
+  if (c->precision != ARP_FP64) return launch_cluster_chain_f32(c, U0, Ge, VT, s, rg);
+  return launch_cluster_chain_prec<double>(c, U0, Ge, VT, s, rg);
 }
 
 arp_status launch_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s) {

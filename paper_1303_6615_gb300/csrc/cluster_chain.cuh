@@ -41,10 +41,10 @@
 namespace arp {
 
 struct ClusterChainArgs {
-  const cd* VT;      // [S][3][K1] e^{dT/2 D} R^H V_n (eigen basis), or null (predictor: V = 0)
-  const cd* U0;      // [3][H] the chain's initial state U_0
-  cd* Ge;            // [S][3][K1] g_n = G(U_n) in the eigen basis, written
-  int S, M, q, own;  // links, nodes, nodes per CTA, wavenumbers per CTA
+  const cd* VT;      // [slices][3][K1] e^{dT/2 D} R^H V_n (eigen basis), or null (predictor: V = 0)
+  const cd* U0;      // [3][H] the chain's initial state U_0 (read when Win is null)
+  cd* Ge;            // [slices][3][K1] g_n = G(U_n) in the eigen basis, written
+  int S, M, q, own;  // links of this launch, nodes, nodes per CTA, wavenumbers per CTA
   int ph_smem;       // node phases staged in shared memory (else read from the table)
   int tmp_smem;      // per-node terms staged for a balanced node sum (else summed per wavenumber)
   double dT;
@@ -52,6 +52,9 @@ struct ClusterChainArgs {
   const double* ss64;
   const double* dhalf;
   const cd* gphase;
+  int n0;            // index of this launch's first link
+  const cd* Win;     // [3][K1] carried state w entering link n0, or null: w from U0
+  cd* Wout;          // [3][K1] carried state w after the last link, or null
 };
 
 template <int LOGN> struct ClusterBlock {
@@ -121,8 +124,14 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
 #pragma unroll
     for (int b = 0; b < 3; ++b) GPH[b * own + (k - k0)] = a.dhalf[k] * a.gphase[b * K1 + k];
   }
-  // w = e^{dT/2 D} R^H U_0 for the own wavenumbers; its float copy into every CTA's WS
+  // w = e^{dT/2 D} R^H U_0 (or the carried w of an earlier launch) for the own
+  // wavenumbers; its float copy into every CTA's WS
   for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
+    if (a.Win) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) W64[b * own + (k - k0)] = a.Win[b * K1 + k];
+      continue;
+    }
     cd x[3], e[3];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
@@ -141,7 +150,7 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
   const int orr = owner_t ? (int)threadIdx.x - ob * no : 0;
   const int ok = k0 + orr;
   auto load_vt = [&](int n) {
-    return (a.VT && owner_t && n < a.S) ? a.VT[((size_t)n * 3 + ob) * K1 + ok] : cd{0.0, 0.0};
+    return (a.VT && owner_t && n < a.S) ? a.VT[((size_t)(a.n0 + n) * 3 + ob) * K1 + ok] : cd{0.0, 0.0};
   };
   cd vt_cur = load_vt(0), vt_nxt = load_vt(1);
   __syncthreads();  // W64
@@ -218,7 +227,7 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
           v = W64[i] + (0.5 * a.dT) * sum;
         } else {  // g = e^{dT/2 D} e^{-(dT/eps) L} (w + dT k2); next w = e^{dT/2 D} g + VT_n
           const cd g = GPH[i] * (W64[i] + a.dT * sum);
-          a.Ge[((size_t)n * 3 + ob) * K1 + ok] = g;
+          a.Ge[((size_t)(a.n0 + n) * 3 + ob) * K1 + ok] = g;
           v = DH[orr] * g + vt_cur;
           W64[i] = v;
           vt_cur = vt_nxt;
@@ -230,6 +239,11 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
       cl.sync();  // 4
     }
   }
+  if (a.Wout)
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += BLOCK) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) a.Wout[b * K1 + k] = W64[b * own + (k - k0)];
+    }
   cl.sync();  // no CTA leaves while another may still store into its shared memory
 }
 
@@ -262,9 +276,10 @@ inline ClusterPlan cluster_plan(int logn, int M, int K1, int C) {
 }
 
 // Launch configuration of `count` clusters of C CTAs of `kern`; true if at
-// least one such cluster can be resident.
+// least one such cluster can be resident (not queried when `known_fit`: the
+// caller has checked this size on the current context's SMs before).
 inline bool cluster_config(const void* kern, int C, int block, size_t smem, int count, cudaStream_t s,
-                           cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+                           cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, bool known_fit = false) {
   if (smem > kMaxSmem) return false;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -283,6 +298,7 @@ inline bool cluster_config(const void* kern, int C, int block, size_t smem, int 
   cfg->stream = s;
   cfg->attrs = attr;
   cfg->numAttrs = 1;
+  if (known_fit) return true;
   int clusters = 0;
   e = cudaOccupancyMaxActiveClusters(&clusters, kern, cfg);
   if (e != cudaSuccess || clusters < 1) {
@@ -296,16 +312,21 @@ inline bool cluster_config(const void* kern, int C, int block, size_t smem, int 
 // finish_body); ARP_EINVAL (nothing launched) if no cluster of 16 or 8 CTAs
 // with this kernel's shared memory can be scheduled.
 template <typename T, int LOGN>
-arp_status launch_cluster_chain_n(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s) {
+arp_status launch_cluster_chain_n(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s,
+                                  const ChainRange* rg) {
   constexpr int BLOCK = ClusterBlock<LOGN>::value;
   const void* kern = (const void*)chain_cluster_kernel<T, LOGN, BLOCK>;
   for (int C : {16, 8}) {
+    if (rg && rg->cluster && rg->cluster != C) continue;
     const ClusterPlan p = cluster_plan<T>(LOGN, c->M, c->K1, C);
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    if (!cluster_config(kern, C, BLOCK, p.smem, 1, s, &cfg, attr)) continue;
-    ClusterChainArgs a{VT, U0, Ge, c->slices, c->M, p.q, p.own, p.ph_smem, p.tmp_smem, c->dT, c->inv_sig64,
-                       c->sk_sig64, c->dhalf, c->gphase};
+    const bool known = rg && rg->cluster == C && !rg->check_only;
+    if (!cluster_config(kern, C, BLOCK, p.smem, 1, s, &cfg, attr, known)) continue;
+    if (rg && rg->check_only) return ARP_OK;
+    ClusterChainArgs a{VT, U0, Ge, rg ? rg->nl : c->slices, c->M, p.q, p.own, p.ph_smem, p.tmp_smem, c->dT,
+                       c->inv_sig64, c->sk_sig64, c->dhalf, c->gphase, rg ? rg->n0 : 0, rg ? rg->Win : nullptr,
+                       rg ? rg->Wout : nullptr};
     NbarTabs<T> tb = nbar_tabs<T>(c);
     void* args[] = {&a, &tb};
     return check_cuda(c, cudaLaunchKernelExC(&cfg, kern, args), "cluster chain: launch");
@@ -314,17 +335,18 @@ arp_status launch_cluster_chain_n(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT
 }
 
 template <typename T>
-arp_status launch_cluster_chain_prec(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s) {
+arp_status launch_cluster_chain_prec(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s,
+                                     const ChainRange* rg) {
   switch (c->logN) {
-    case 3: return launch_cluster_chain_n<T, 3>(c, U0, Ge, VT, s);
-    case 4: return launch_cluster_chain_n<T, 4>(c, U0, Ge, VT, s);
-    case 5: return launch_cluster_chain_n<T, 5>(c, U0, Ge, VT, s);
-    case 6: return launch_cluster_chain_n<T, 6>(c, U0, Ge, VT, s);
-    case 7: return launch_cluster_chain_n<T, 7>(c, U0, Ge, VT, s);
-    case 8: return launch_cluster_chain_n<T, 8>(c, U0, Ge, VT, s);
-    case 9: return launch_cluster_chain_n<T, 9>(c, U0, Ge, VT, s);
-    case 10: return launch_cluster_chain_n<T, 10>(c, U0, Ge, VT, s);
-    case 11: return launch_cluster_chain_n<T, 11>(c, U0, Ge, VT, s);
+    case 3: return launch_cluster_chain_n<T, 3>(c, U0, Ge, VT, s, rg);
+    case 4: return launch_cluster_chain_n<T, 4>(c, U0, Ge, VT, s, rg);
+    case 5: return launch_cluster_chain_n<T, 5>(c, U0, Ge, VT, s, rg);
+    case 6: return launch_cluster_chain_n<T, 6>(c, U0, Ge, VT, s, rg);
+    case 7: return launch_cluster_chain_n<T, 7>(c, U0, Ge, VT, s, rg);
+    case 8: return launch_cluster_chain_n<T, 8>(c, U0, Ge, VT, s, rg);
+    case 9: return launch_cluster_chain_n<T, 9>(c, U0, Ge, VT, s, rg);
+    case 10: return launch_cluster_chain_n<T, 10>(c, U0, Ge, VT, s, rg);
+    case 11: return launch_cluster_chain_n<T, 11>(c, U0, Ge, VT, s, rg);
     default: return fail(c, ARP_EINVAL, "cluster chain: unsupported grid size");
   }
 }

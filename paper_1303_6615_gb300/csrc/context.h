@@ -11,6 +11,7 @@
 
 namespace arp {
 struct DftWork;  // dftgemm.cu: DFT matrices, GEMM operands, cuBLAS handle
+struct Pipe;     // pipeline.cu: SM partition, streams and events of the pipelined solve
 }
 
 struct arp_ctx {
@@ -70,6 +71,9 @@ struct arp_ctx {
   int coarse_grid = 0;           // ARP_OPT_COARSE_GRID: 0 = the fine grid, else N_c < N for the coarse chain
   arp_ctx* coarse = nullptr;     // owned sub-context on the N_c grid (its tables, chain buffers), made on first use
   arp::DftWork* dft = nullptr;   // ARP_TF32X3 / ARP_BF16X2 workspace, made on first use
+  int pipeline = 1;              // ARP_OPT_PIPELINE: 0 off, 1 automatic chunks, n >= 2 links per chunk
+  arp::Pipe* pipe = nullptr;     // made by the first pipelined solve
+  int last_pipelined = 0;        // whether the last arp_parareal_solve ran pipelined
   int level = -1;                // -1: no initial state; 0: predictor pending
   bool have_initial = false;
 
@@ -114,8 +118,22 @@ arp_status coarse_step(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_
 // launching) if the grid cannot be co-resident.
 arp_status launch_chain(arp_ctx* c, cd* U, cd* Gc, const cd* V, cudaStream_t s);
 // The same chain inside one thread-block cluster (no grid barriers).  Returns
-// ARP_EINVAL (without launching) if no suitable cluster can be scheduled.
-arp_status launch_cluster_chain(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s);
+// ARP_EINVAL (without launching) if no suitable cluster can be scheduled.  With
+// a range, only links n0 .. n0+nl-1 run: the carried eigen-basis state enters
+// from Win (null: from U0) and is stored to Wout (if not null), so consecutive
+// ranges give the whole chain's results bit for bit; check_only launches
+// nothing and reports whether a cluster fits on the current context's SMs.
+// cluster: 0 tries 16 then 8 CTAs, else only that size, already known to fit
+// the current context's SMs (no occupancy query).
+struct ChainRange {
+  int n0 = 0, nl = 0;
+  const cd* Win = nullptr;
+  cd* Wout = nullptr;
+  bool check_only = false;
+  int cluster = 0;
+};
+arp_status launch_cluster_chain(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, cudaStream_t s,
+                                const ChainRange* rg = nullptr);
 
 // parareal.cu
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);
@@ -123,6 +141,13 @@ arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* cha
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s);
 // api.cu: the coarse-grid sub-context, created or refreshed to match c's options.
 arp_status ensure_coarse(arp_ctx* c, cudaStream_t s);
+// pipeline.cu: arp_parareal_solve with the levels overlapped (the same results
+// bit for bit); *ran false (nothing done) where the SM partition or the chain
+// cluster is unavailable.
+bool pipeline_eligible(const arp_ctx* c);
+arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, int* k_done, double* change);
+arp_status pipeline_info(const arp_ctx* c, int* out);
+void pipeline_release(arp_ctx* c);
 // dftgemm.cu: the DFT-as-GEMM precisions (ARP_TF32X3, ARP_BF16X2): the time
 // average's node terms as one chunk partial [batch][1][3][K1], and the ETDRK4
 // fine sweep with all states stepped together.
