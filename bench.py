@@ -43,7 +43,7 @@ FP64_ALU_PEAK_TFLOPS = 1.25
 CPU_SAMPLE_SLICES = 64          # cpu_baseline sample (about 10 s of oracle work)
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fine-sweep kernel on this workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
-FINE_TRAFFIC_BYTES = {"fp32": 2257408, "fp64": None}
+FINE_TRAFFIC_BYTES = {"fp32": 2256896, "fp64": None}
 REFERENCE_SAMPLE_SLICES = 8     # per-step sample of the reference arm
 
 
@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper", "schemes",
-                                       "coarsegrid", "dftgemm"],
+                                       "coarsegrid", "dftgemm", "kernels"],
                     default="headline",
                     help="headline: the contract line (default); tts: time to 1e-5 relative error against the "
                          "serial fine solution (FP64 sweeps on the GPU), FP32 bulk vs FP64; precision: the N=1024 precision sweep; "
@@ -87,7 +87,9 @@ def parse():
                          "experiments of Sec. 6.2 (Eq. 6.4 initial condition, eps = 1e-2, 1e-1, 1), asymptotic "
                          "and standard parareal; schemes: the three fine solvers' sweep throughput and "
                          "accuracy against the step size; coarsegrid: the coarse solver on N/2 and N/4 points; "
-                         "dftgemm: the DFT-as-GEMM precisions against the FFT path")
+                         "dftgemm: the DFT-as-GEMM precisions against the FFT path; kernels: the predictor and "
+                         "one level-by-level iteration of the headline workload (the whole-sweep fine launch and "
+                         "the whole-chain cluster launch), a case for profilers")
     ap.add_argument("--instances", type=int, default=1024)
     ap.add_argument("--probe", action="store_true",
                     help="with --mode dftgemm: only one small time average (a case sized for a profiler)")
@@ -441,17 +443,21 @@ def run_tts(args) -> dict:
                 if e <= 1e-5 and kstar is None:
                     kstar = k
                     break
+            # timed: the solve a user makes once K is known (pipelined where it applies)
+            b.arp_set_option(s.ctx, b.ARP_OPT_KMAX, kstar if kstar is not None else kcap)
             times = []
             for _ in range(3):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 b.arp_set_initial(s.ctx, u0h)
-                for _k in range((kstar if kstar is not None else kcap) + 1):
-                    b.arp_parareal_iterate(s.ctx)
+                b.arp_parareal_solve(s.ctx)
                 b.arp_get_slices(s.ctx, Uh)
                 torch.cuda.synchronize()
                 times.append(time.perf_counter() - t0)
-        out[name] = {"k_star": kstar, "errors_per_k": errs, "seconds": min(times)}
+            e = float(np.max(_parseval(Uh.numpy()[1:] - ref[1:]) / _parseval(ref[1:])))
+            pinfo = b.arp_pipeline_info(s.ctx)
+        out[name] = {"k_star": kstar, "errors_per_k": errs, "seconds": min(times), "solve_error": e,
+                     "pipelined": bool(pinfo["pipelined"])}
     if out["fp64"]["k_star"] is not None and out["fp32"]["k_star"] is not None:
         out["speedup_fp32_vs_fp64"] = out["fp64"]["seconds"] / out["fp32"]["seconds"]
     return out
@@ -929,6 +935,26 @@ def run_serve(args) -> dict:
     return out
 
 
+def run_kernels(args) -> dict:
+    """The headline workload's two dominant kernels in their level-by-level
+    launches (ARP_OPT_PIPELINE 0): the predictor's chain (one cluster launch
+    over all 256 links), then one iteration: the fine sweep of all 256
+    slices in one launch, the correction, the chain, the norm."""
+    import torch
+
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import build as bld
+    bld.build()
+    w = WORKLOAD
+    prec = b.ARP_FP32 if args.precision == "fp32" else b.ARP_FP64
+    with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
+        b.arp_set_option(s.ctx, b.ARP_OPT_PIPELINE, 0)
+        b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+        b.arp_parareal_iterate(s.ctx)
+        k, ch = b.arp_parareal_iterate(s.ctx)
+    return {"mode": "kernels", "workload": w.name, "precision": args.precision, "level": k, "change": ch}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -939,7 +965,7 @@ def main():
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             res = {"tts": run_tts, "precision": run_precision, "batched": run_batched, "serve": run_serve,
                    "paper": run_paper, "schemes": run_schemes, "coarsegrid": run_coarsegrid,
-                   "dftgemm": run_dftgemm}[args.mode](args)
+                   "dftgemm": run_dftgemm, "kernels": run_kernels}[args.mode](args)
             print(json.dumps(res), flush=True)
         return
     if args.impl == "reference":
