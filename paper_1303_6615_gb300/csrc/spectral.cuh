@@ -60,17 +60,36 @@ __device__ __forceinline__ void phys_to_eigen(const cpx<T> u[3], T is, T ss, cpx
   a[0] = r2 * (u[0] - iv2 - hs);
 }
 
-// Padded position of element i of a lane array: one slot every 2^kShift elements.
+// Position of element i in a lane array of N points.  FP32 lanes of N >= 128
+// points are not padded but XOR-swizzled inside each aligned 16-element block:
+// bits 0-3 of i are XORed with S(bits 4-6 of i), S linear over GF(2) with bit
+// 4 -> 0011, bit 5 -> 0110, bit 6 -> 1001.  Each half-warp access of the
+// radix-8 stages varies four address bits: bits 0-3 for spans >= 128, bits
+// {0,1,2,6}, {0,1,5,6} or {0,4,5,6} for spans 64, 32, 16; the middle stage
+// varies {3,4,5,6}, {2,3,4,5} or {1,2,3,4}; for every such set the swizzled
+// bits 0-3 are an invertible function of the varying bits, so the 16 threads
+// hit 16 different bank pairs.  Other lanes (FP64, and FP32 below 128 points,
+// where lanes of several states share a warp) keep one padding slot every
+// 2^kShift elements.
 template <typename T> struct Pad;
 template <> struct Pad<float> { static constexpr int kShift = 4; };
 template <> struct Pad<double> { static constexpr int kShift = 3; };
 template <typename T>
+__host__ __device__ constexpr bool swizzled_lanes(int n) {
+  return sizeof(T) == 4 && n >= 128;
+}
+template <typename T, int N>
 __host__ __device__ __forceinline__ constexpr int pidx(int i) {
-  return i + (i >> Pad<T>::kShift);
+  if constexpr (swizzled_lanes<T>(N)) {
+    // S(b) for b = 0..7, one nibble each: 0, 3, 6, 5, 9, 10, 15, 12
+    return i ^ (int)((0xCFA95630u >> (((unsigned)i >> 2) & 28u)) & 15u);
+  } else {
+    return i + (i >> Pad<T>::kShift);
+  }
 }
 template <typename T>
 __host__ __device__ constexpr int padded_len(int n) {
-  return n + (n >> Pad<T>::kShift);
+  return swizzled_lanes<T>(n) ? n : n + (n >> Pad<T>::kShift);
 }
 
 // Stage plan for N = 2^LOGN: middle span 2^kLogMid (8 if 3 | log2 N, else 2
@@ -101,10 +120,10 @@ __device__ __forceinline__ void pack_mode(cpx<T>* Z0, cpx<T>* Z1, int k, const c
     Z0[0] = mk<T>(A.x, D.x);
     Z1[0] = mk<T>((T)0, (T)0);
   } else {
-    Z0[pidx<T>(k)] = A + mul_i(D);
-    Z0[pidx<T>(N - k)] = conj(A) + mul_i(conj(D));
-    Z1[pidx<T>(k)] = B + mul_i(C);
-    Z1[pidx<T>(N - k)] = conj(B) + mul_i(conj(C));
+    Z0[pidx<T, N>(k)] = A + mul_i(D);
+    Z0[pidx<T, N>(N - k)] = conj(A) + mul_i(conj(D));
+    Z1[pidx<T, N>(k)] = B + mul_i(C);
+    Z1[pidx<T, N>(N - k)] = conj(B) + mul_i(conj(C));
   }
 }
 
@@ -112,10 +131,10 @@ __device__ __forceinline__ void pack_mode(cpx<T>* Z0, cpx<T>* Z1, int k, const c
 template <typename T, int N>
 __device__ __forceinline__ void zero_mode(cpx<T>* Z0, cpx<T>* Z1, int k) {
   const cpx<T> z = mk<T>(0, 0);
-  Z0[pidx<T>(k)] = z;
-  Z1[pidx<T>(k)] = z;
-  Z0[pidx<T>(N - k)] = z;
-  Z1[pidx<T>(N - k)] = z;
+  Z0[pidx<T, N>(k)] = z;
+  Z1[pidx<T, N>(k)] = z;
+  Z0[pidx<T, N>(N - k)] = z;
+  Z1[pidx<T, N>(N - k)] = z;
 }
 
 // Reads the forward-transform output at wavenumber k (0 <= k <= K) and returns
@@ -130,9 +149,9 @@ __device__ __forceinline__ void unpack_mode(const cpx<T>* Z0, const cpx<T>* Z1, 
     n3[1] = mk<T>(q.y * inv_n, 0);
     n3[2] = mk<T>(0, 0);
   } else {
-    cpx<T> q = Z0[pidx<T>(k)];
-    cpx<T> qm = conj(Z0[pidx<T>(N - k)]);
-    cpx<T> r = Z1[pidx<T>(k)];
+    cpx<T> q = Z0[pidx<T, N>(k)];
+    cpx<T> qm = conj(Z0[pidx<T, N>(N - k)]);
+    cpx<T> r = Z1[pidx<T, N>(k)];
     const T half_n = (T)0.5 * inv_n;
     n3[0] = half_n * (q + qm);
     n3[1] = half_n * mul_mi(q - qm);
@@ -193,7 +212,7 @@ __device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>
     const int base = ((bidx >> (logL - 3)) << logL) + j;
     cpx<T> x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = Zl[pidx<T>(base + q * e)];
+    for (int q = 0; q < 8; ++q) x[q] = Zl[pidx<T, N>(base + q * e)];
     if (!DIF && j) {
 #pragma unroll
       for (int q = 1; q < 8; ++q) x[q] = x[q] * tw[(q - 1) * e + j];
@@ -204,7 +223,7 @@ __device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>
       for (int q = 1; q < 8; ++q) x[q] = x[q] * conj(tw[(q - 1) * e + j]);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) Zl[pidx<T>(base + q * e)] = x[q];
+    for (int q = 0; q < 8; ++q) Zl[pidx<T, N>(base + q * e)] = x[q];
   }
 }
 
@@ -233,8 +252,8 @@ __device__ __forceinline__ void middle_stage(cpx<T>* Z, int npairs) {
     cpx<T> a[8], b[8];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      a[q] = Z0[pidx<T>(R * i + q)];
-      b[q] = Z1[pidx<T>(R * i + q)];
+      a[q] = Z0[pidx<T, N>(R * i + q)];
+      b[q] = Z1[pidx<T, N>(R * i + q)];
     }
     if (R == 8) {
       dft8<T, +1>(a);
@@ -260,8 +279,8 @@ __device__ __forceinline__ void middle_stage(cpx<T>* Z, int npairs) {
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      Z0[pidx<T>(R * i + q)] = a[q];
-      Z1[pidx<T>(R * i + q)] = b[q];
+      Z0[pidx<T, N>(R * i + q)] = a[q];
+      Z1[pidx<T, N>(R * i + q)] = b[q];
     }
   }
 }
