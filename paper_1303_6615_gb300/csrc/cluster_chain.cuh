@@ -166,8 +166,9 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
 #pragma unroll 1
     for (int round = 0; round < 2; ++round) {
       // 1: this CTA's nodes, all at once
-      for (int item = threadIdx.x; item < nq * (N / 2 + 1); item += BLOCK) {
-        const int d = item / (N / 2 + 1), k = item - d * (N / 2 + 1);
+      constexpr int ZE1 = zero_end<N>() + 1;
+      for (int item = threadIdx.x; item < nq * ZE1; item += BLOCK) {
+        const int d = item / ZE1, k = item - d * ZE1;
         cpx<T>* Z0 = Z + 2 * d * PL;
         if (k > K) {
           zero_mode<T, N>(Z0, Z0 + PL, k);

@@ -38,7 +38,7 @@ __device__ __forceinline__ void nbar_nodes(const cpx<T>* WS, cpx<T>* ACC, int m0
   constexpr int N = 1 << LOGN;
   constexpr int K = (N - 1) / 3;
   constexpr int K1 = K + 1;
-  for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
+  for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK) {
     if (k > K) {
       zero_mode<T, N>(Z0, Z1, k);
       continue;
@@ -57,7 +57,7 @@ __device__ __forceinline__ void nbar_nodes(const cpx<T>* WS, cpx<T>* ACC, int m0
     nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
     const bool next = (m + 1 < m1);
     const T wm = tb.avg.weight[m];
-    for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
+    for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK) {
       if (k > K) {
         if (next) zero_mode<T, N>(Z0, Z1, k);
         continue;

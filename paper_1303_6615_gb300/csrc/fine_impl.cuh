@@ -141,7 +141,7 @@ __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restr
   const cd* src = in + (size_t)slice * 3 * H;
   if (kTwShared)
     for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TWs[t] = tb.tw[t];
-  for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
+  for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK) {
     if (k <= K) {
       const T is = tb.is[k], ss = tb.ss[k];
       IS[k] = is;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restr
     for (int stage = 0; stage < 4; ++stage) {
       nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
       const bool pack_next = !(last && stage == 3);
-      for (int k = threadIdx.x; k <= N / 2; k += BLOCK) {
+      for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK) {
         if (k > K) {
           if (pack_next) zero_mode<T, N>(Z0, Z1, k);
           continue;
@@ -351,7 +351,7 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
       pack_mode<T, N>(Z0, Z1, k, u[r], is, ss);
     }
   }
-  for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+  for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
   __syncthreads();
 
   const EtdView<T> e = tb.etd;
@@ -405,7 +405,7 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
         if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
       }
       if (pack_next)
-        for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+        for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
       __syncthreads();
     }
   }

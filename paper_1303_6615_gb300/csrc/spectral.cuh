@@ -92,6 +92,17 @@ __host__ __device__ constexpr int padded_len(int n) {
   return swizzled_lanes<T>(n) ? n : n + (n >> Pad<T>::kShift);
 }
 
+// Last wavenumber whose bins k and N-k must be zero before an inverse
+// transform.  The first outer inverse stage (span N) reads bin j + q N/8 as its
+// q-th input; the 2/3 rule leaves bins 3N/8 .. 5N/8-1 (q = 3, 4) zero, so that
+// stage takes them as zero without reading them, and only K < k <= 3N/8 (the
+// partner N-k = 5N/8 is a q = 5 input) must be cleared.  Without outer stages
+// (N = 8) every bin is read.
+template <int N>
+__host__ __device__ constexpr int zero_end() {
+  return (N > 8) ? 3 * N / 8 : N / 2;
+}
+
 // Stage plan for N = 2^LOGN: middle span 2^kLogMid (8 if 3 | log2 N, else 2
 // or 4), outer radix-8 stages at spans 2^logL, logL = LOGN, LOGN-3, ... > kLogMid.
 __host__ __device__ constexpr int stage_log_mid(int logn) { return (logn % 3 == 0) ? 3 : logn % 3; }
@@ -194,12 +205,38 @@ __device__ __forceinline__ void dft8(cpx<T> x[8]) {
   x[7] = e3 - t3;
 }
 
+// dft8 with x[3] = x[4] = 0: the even half's a0 = a1 = x[0] and the odd half's
+// a2 = x[7], a3 = -(sign i) x[7]; the rest as dft8 (the same roundings).
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft8_in34zero(cpx<T> x[8]) {
+  const cpx<T> ea2 = x[2] + x[6];
+  const cpx<T> ea3 = SIGN > 0 ? mul_i(x[2] - x[6]) : mul_mi(x[2] - x[6]);
+  const cpx<T> e0 = x[0] + ea2, e2 = x[0] - ea2, e1 = x[0] + ea3, e3 = x[0] - ea3;
+  const cpx<T> oa0 = x[1] + x[5], oa1 = x[1] - x[5];
+  const cpx<T> oa3 = SIGN > 0 ? mul_mi(x[7]) : mul_i(x[7]);
+  const cpx<T> o0 = oa0 + x[7], o2 = oa0 - x[7], o1 = oa1 + oa3, o3 = oa1 - oa3;
+  const T r = Consts<T>::rsqrt2();
+  const cpx<T> t1 = SIGN > 0 ? r * (o1 + mul_i(o1)) : r * (o1 - mul_i(o1));
+  const cpx<T> t2 = SIGN > 0 ? mul_i(o2) : mul_mi(o2);
+  const cpx<T> t3 = SIGN > 0 ? r * (mul_i(o3) - o3) : r * (mk<T>(-o3.x, -o3.y) - mul_i(o3));
+  x[0] = e0 + o0;
+  x[4] = e0 - o0;
+  x[1] = e1 + t1;
+  x[5] = e1 - t1;
+  x[2] = e2 + t2;
+  x[6] = e2 - t2;
+  x[3] = e3 + t3;
+  x[7] = e3 - t3;
+}
+
 // One outer radix-8 stage on `nlanes` lanes stored back to back (lane l at
 // Z + l * padded_len(N)), span L = 2^logL (L/8 butterflies per group).
 // tw: this stage's table, tw[(q-1) L/8 + j] = e^{-2 pi i q j / L}.
 // DIF (inverse, sign +): DFT then multiply by conj(tw); DIT (forward, sign -):
-// multiply by tw then DFT.
-template <typename T, int N, int BLOCK, int SIGN, bool DIF>
+// multiply by tw then DFT.  PRUNE (span N only, see zero_end): 1 = inputs
+// q = 3, 4 are zero and not read; 2 = outputs q = 3, 4 are never read and not
+// stored (their arithmetic drops out).
+template <typename T, int N, int BLOCK, int SIGN, bool DIF, int PRUNE = 0>
 __device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>* tw, int logL) {
   constexpr int PL = padded_len<T>(N);
   constexpr int NB = N / 8;
@@ -212,18 +249,27 @@ __device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>
     const int base = ((bidx >> (logL - 3)) << logL) + j;
     cpx<T> x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = Zl[pidx<T, N>(base + q * e)];
+    for (int q = 0; q < 8; ++q) {
+      if (PRUNE == 1 && (q == 3 || q == 4)) continue;
+      x[q] = Zl[pidx<T, N>(base + q * e)];
+    }
     if (!DIF && j) {
 #pragma unroll
       for (int q = 1; q < 8; ++q) x[q] = x[q] * tw[(q - 1) * e + j];
     }
-    dft8<T, SIGN>(x);
+    if (PRUNE == 1)
+      dft8_in34zero<T, SIGN>(x);
+    else
+      dft8<T, SIGN>(x);
     if (DIF && j) {
 #pragma unroll
       for (int q = 1; q < 8; ++q) x[q] = x[q] * conj(tw[(q - 1) * e + j]);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) Zl[pidx<T, N>(base + q * e)] = x[q];
+    for (int q = 0; q < 8; ++q) {
+      if (PRUNE == 2 && (q == 3 || q == 4)) continue;
+      Zl[pidx<T, N>(base + q * e)] = x[q];
+    }
   }
 }
 
@@ -292,16 +338,26 @@ template <typename T, int LOGN, int BLOCK>
 __device__ __forceinline__ void nonlinear_transform(cpx<T>* Z, int nstates, const cpx<T>* TW) {
   constexpr int N = 1 << LOGN;
   constexpr int LOGMID = stage_log_mid(LOGN);
+  if constexpr (LOGN > LOGMID) {
+    // span N first: bins 3N/8 .. 5N/8-1 are zero by the 2/3 rule
+    radix8_stage<T, N, BLOCK, +1, true, 1>(Z, 2 * nstates, TW + twiddle_offset(LOGN, LOGN), LOGN);
+    __syncthreads();
+  }
 #pragma unroll
-  for (int logL = LOGN; logL > LOGMID; logL -= 3) {
+  for (int logL = LOGN - 3; logL > LOGMID; logL -= 3) {
     radix8_stage<T, N, BLOCK, +1, true>(Z, 2 * nstates, TW + twiddle_offset(LOGN, logL), logL);
     __syncthreads();
   }
   middle_stage<T, LOGN, BLOCK>(Z, nstates);
   __syncthreads();
 #pragma unroll
-  for (int logL = LOGMID + 3; logL <= LOGN; logL += 3) {
+  for (int logL = LOGMID + 3; logL < LOGN; logL += 3) {
     radix8_stage<T, N, BLOCK, -1, false>(Z, 2 * nstates, TW + twiddle_offset(LOGN, logL), logL);
+    __syncthreads();
+  }
+  if constexpr (LOGN > LOGMID) {
+    // span N last: bins 3N/8 .. 5N/8-1 lie above the kept modes and are not read
+    radix8_stage<T, N, BLOCK, -1, false, 2>(Z, 2 * nstates, TW + twiddle_offset(LOGN, LOGN), LOGN);
     __syncthreads();
   }
 }

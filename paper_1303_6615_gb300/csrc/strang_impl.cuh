@@ -83,7 +83,7 @@ __device__ __forceinline__ void strang_stage(cpx<T>* Z0, const cpx<T>* TW, const
     for (int q = 0; q < 3; ++q) x[q] = w[r][q] + ((T)0.5 * h) * k1[r][q];
     pack_mode<T, N>(Z0, Z1, k, x, IS[k], SS[k]);
   }
-  for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+  for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
   __syncthreads();
   nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);
 #pragma unroll
@@ -143,7 +143,7 @@ __device__ __forceinline__ void strang_body(const cd* __restrict__ in, cd* __res
     }
     pack_mode<T, N>(Z0, Z1, k, w[r], tb.is[k], tb.ss[k]);
   }
-  for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+  for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
   __syncthreads();
 
   const T h = (T)tb.h;
@@ -168,7 +168,7 @@ __device__ __forceinline__ void strang_body(const cd* __restrict__ in, cd* __res
       }
       pack_mode<T, N>(Z0, Z1, k, w[r], IS[k], SS[k]);
     }
-    for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+    for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
     __syncthreads();
   }
 
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(BLOCK) strang_chain_kernel(cd* __restrict__ U,
       }
       pack_mode<T, N>(Z0, Z1, k, w[r], IS[k], SS[k]);
     }
-    for (int k = K1 + threadIdx.x; k <= N / 2; k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+    for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
     __syncthreads();
     strang_stage<T, LOGN, BLOCK, MPT>(Z0, TW, IS, SS, w, wlo, (T)tb.h);
 #pragma unroll
