@@ -947,12 +947,20 @@ def run_kernels(args) -> dict:
     bld.build()
     w = WORKLOAD
     prec = b.ARP_FP32 if args.precision == "fp32" else b.ARP_FP64
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
         b.arp_set_option(s.ctx, b.ARP_OPT_PIPELINE, 0)
         b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+        torch.cuda.synchronize()
+        ev[0].record()
         b.arp_parareal_iterate(s.ctx)
+        ev[1].record()
         k, ch = b.arp_parareal_iterate(s.ctx)
-    return {"mode": "kernels", "workload": w.name, "precision": args.precision, "level": k, "change": ch}
+        ev[2].record()
+        torch.cuda.synchronize()
+    return {"mode": "kernels", "workload": w.name, "precision": args.precision, "level": k, "change": ch,
+            "predictor_ms": ev[0].elapsed_time(ev[1]), "iteration_ms": ev[1].elapsed_time(ev[2]),
+            "note": "first calls of a new context (cold caches, kernel loading); for profilers, not a benchmark"}
 
 
 def main():
