@@ -43,7 +43,7 @@ FP64_ALU_PEAK_TFLOPS = 1.25
 CPU_SAMPLE_SLICES = 64          # cpu_baseline sample (about 10 s of oracle work)
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fine-sweep kernel on this workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
-FINE_TRAFFIC_BYTES = {"fp32": None, "fp64": None}
+FINE_TRAFFIC_BYTES = {"fp32": 2259456, "fp64": None}
 REFERENCE_SAMPLE_SLICES = 8     # per-step sample of the reference arm
 
 
@@ -950,7 +950,12 @@ def run_kernels(args) -> dict:
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
         b.arp_set_option(s.ctx, b.ARP_OPT_PIPELINE, 0)
-        b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+        u0 = torch.from_numpy(w.initial_state()).cuda()
+        for timed in (False, True):
+            b.arp_set_initial(s.ctx, u0)
+            if not timed:
+                b.arp_parareal_iterate(s.ctx)
+                b.arp_parareal_iterate(s.ctx)
         torch.cuda.synchronize()
         ev[0].record()
         b.arp_parareal_iterate(s.ctx)
@@ -960,7 +965,7 @@ def run_kernels(args) -> dict:
         torch.cuda.synchronize()
     return {"mode": "kernels", "workload": w.name, "precision": args.precision, "level": k, "change": ch,
             "predictor_ms": ev[0].elapsed_time(ev[1]), "iteration_ms": ev[1].elapsed_time(ev[2]),
-            "note": "first calls of a new context (cold caches, kernel loading); for profilers, not a benchmark"}
+            "note": "one timed pass after one warm-up pass; a case for profilers, not the benchmark"}
 
 
 def main():
