@@ -42,7 +42,7 @@ struct DftWork {
   int tables_prec = -1;    // precision the DFT matrices were split for
   // fine sweep state, [slices][3][K1] each
   int fine_cap = 0;
-  cf *U = nullptr, *ULO = nullptr, *NU = nullptr, *A1 = nullptr, *ACC = nullptr, *ACCLO = nullptr, *XS = nullptr;
+  cf *U = nullptr, *ULO = nullptr, *NU = nullptr, *A1 = nullptr, *ACC = nullptr, *XS = nullptr;
 };
 
 namespace {
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(32 * kAvgChunks) dft_unpack_avg_kernel(
 // that stage (the formulas of the FP32 fine sweep, float-pair state and update
 // sum), writing the next stage's input XS.
 __global__ void dft_fine_stage_kernel(const float* __restrict__ Q, int S_, int K, int R, int stage,
-                                      FineTabs<float> tb, cf* U, cf* ULO, cf* NU, cf* A1, cf* ACC, cf* ACCLO,
+                                      FineTabs<float> tb, cf* U, cf* ULO, cf* NU, cf* A1, cf* ACC,
                                       cf* XS) {
   const int K1 = K + 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,14 +216,13 @@ __global__ void dft_fine_stage_kernel(const float* __restrict__ Q, int S_, int K
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const size_t o = ((size_t)s * 3 + q) * K1 + k;
-    cf u = U[o], ulo = ULO[o], nu = NU[o], a1 = A1[o], acc = ACC[o], acclo = ACCLO[o];
-    XS[o] = etd32_stage(stage, q * K1 + k, bn[q], u, ulo, nu, a1, acc, acclo, tb.etd, tb.E_lo);
+    cf u = U[o], ulo = ULO[o], nu = NU[o], a1 = A1[o], acc = ACC[o];
+    XS[o] = etd32_stage(stage, q * K1 + k, bn[q], u, ulo, nu, a1, acc, tb.etd, tb.E_lo);
     U[o] = u;
     ULO[o] = ulo;
     NU[o] = nu;
     A1[o] = a1;
     ACC[o] = acc;
-    ACCLO[o] = acclo;
   }
 }
 
@@ -351,7 +350,7 @@ arp_status ensure_work(arp_ctx* c, size_t cols, int fine, cudaStream_t s) {
     d->cols = cols;
   }
   if (fine > d->fine_cap) {
-    cf** arrs[7] = {&d->U, &d->ULO, &d->NU, &d->A1, &d->ACC, &d->ACCLO, &d->XS};
+    cf** arrs[6] = {&d->U, &d->ULO, &d->NU, &d->A1, &d->ACC, &d->XS};
     for (cf** a : arrs) {
       void* p = *a;
       if ((r = grow(p, (size_t)fine * 3 * c->K1 * sizeof(cf))) != ARP_OK) return r;
@@ -417,7 +416,7 @@ arp_status dft_fine_t(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t
       if ((r = check_cuda(c, cudaGetLastError(), "dft fine: pack")) != ARP_OK) return r;
       if ((r = dft_transforms<S>(c, batch, s)) != ARP_OK) return r;
       dft_fine_stage_kernel<<<blocks_for(n, 128), 128, 0, s>>>(d->Q, batch, c->K, d->R, stage, tb, d->U, d->ULO,
-                                                                d->NU, d->A1, d->ACC, d->ACCLO, d->XS);
+                                                                d->NU, d->A1, d->ACC, d->XS);
       if ((r = check_cuda(c, cudaGetLastError(), "dft fine: stage")) != ARP_OK) return r;
     }
   }
@@ -446,7 +445,7 @@ void dft_release(arp_ctx* c) {
   DftWork* d = c->dft;
   if (!d) return;
   void* ptrs[] = {d->Winv[0], d->Winv[1], d->Wfwd[0], d->Wfwd[1], d->A[0], d->A[1], d->X, d->P[0], d->P[1], d->Q,
-                  d->U, d->ULO, d->NU, d->A1, d->ACC, d->ACCLO, d->XS};
+                  d->U, d->ULO, d->NU, d->A1, d->ACC, d->XS};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (d->blas) cublasDestroy(d->blas);

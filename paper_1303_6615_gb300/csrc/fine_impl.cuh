@@ -71,7 +71,7 @@ template <int LOGN> struct FineBlockAlt {
 
 template <typename T>
 constexpr int fine_mode_arrays() {
-  return std::is_same<T, float>::value ? 6 : 4;  // u, N(u), a1, acc (+ u_lo, acc_lo)
+  return std::is_same<T, float>::value ? 5 : 4;  // u, N(u), a1, acc (+ u_lo)
 }
 
 // Shared memory of one state's transform: two padded lanes and the twiddle tables.
@@ -134,8 +134,7 @@ __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restr
   constexpr bool kPair = std::is_same<T, float>::value;
   static_assert(!(kPair && SCHEME != kSchemeEtdrk4), "the FP32 schemes run in fine_f32_body");
   cpx<T>* ULO = ACC + 3 * K1;                       // FP32 path only
-  cpx<T>* ACCLO = ULO + (kPair ? 3 * K1 : 0);       // FP32 path only
-  T* IS = reinterpret_cast<T*>(ACC + 3 * K1 + (kPair ? 6 * K1 : 0));
+  T* IS = reinterpret_cast<T*>(ACC + 3 * K1 + (kPair ? 3 * K1 : 0));
   T* SS = IS + K1;
 
   const cd* src = in + (size_t)slice * 3 * H;
@@ -182,28 +181,22 @@ __device__ __forceinline__ void fine_body(const cd* __restrict__ in, cd* __restr
         for (int q = 0; q < 3; ++q) {
           const int i = q * K1 + k;
           if constexpr (kPair) {
+            // as etd32_stage, with the state in shared memory
             if (stage == 0) {
               const cf u = U[i];
               NU[i] = bn[q];
+              ACC[i] = ldgc(e.f1 + i) * bn[q];
               const cf a = ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn[q];
               A1[i] = a;
-              const cdf acc = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(tb.E_lo + i), u, ULO[i]), ldgc(e.f1 + i) * bn[q]);
-              ACC[i] = mk<float>(acc.re.hi, acc.im.hi);
-              ACCLO[i] = mk<float>(acc.re.lo, acc.im.lo);
               nx[q] = a;
             } else if (stage == 3) {
-              const cf t = ldgc(e.f3 + i) * bn[q];
-              const cf ah = ACC[i], al = ACCLO[i];
-              const df re = df_add_f(df{ah.x, al.x}, t.x), im = df_add_f(df{ah.y, al.y}, t.y);
-              U[i] = mk<float>(re.hi, im.hi);
-              ULO[i] = mk<float>(re.lo, im.lo);
+              const cdf s = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(tb.E_lo + i), U[i], ULO[i]),
+                                    ACC[i] + ldgc(e.f3 + i) * bn[q]);
+              U[i] = mk<float>(s.re.hi, s.im.hi);
+              ULO[i] = mk<float>(s.re.lo, s.im.lo);
               nx[q] = U[i];
             } else {
-              const cf t = ldgc(e.f2x2 + i) * bn[q];
-              const cf ah = ACC[i], al = ACCLO[i];
-              const df re = df_add_f(df{ah.x, al.x}, t.x), im = df_add_f(df{ah.y, al.y}, t.y);
-              ACC[i] = mk<float>(re.hi, im.hi);
-              ACCLO[i] = mk<float>(re.lo, im.lo);
+              ACC[i] = ACC[i] + ldgc(e.f2x2 + i) * bn[q];
               nx[q] = (stage == 1) ? ldgc(e.E2 + i) * U[i] + ldgc(e.Q + i) * bn[q]
                                    : ldgc(e.E2 + i) * A1[i] + ldgc(e.Q + i) * ((T)2 * bn[q] - NU[i]);
             }
@@ -284,32 +277,28 @@ struct F32Layout {
 };
 
 // One ETDRK4 stage of the FP32 path for one (wavenumber, branch) entry i of the
-// tables: given N of the stage's input (bn), update (in place) the float-pair
-// state u/ulo, N(u), a1 and the float-pair update sum acc/acclo, and return the
-// next stage's input.  Shared by the register-resident sweep and the lock-step
-// DFT-GEMM sweep so both apply the same arithmetic.
+// tables: given N of the stage's input (bn), update N(u), a1 and the stage sum
+// acc, at the last stage the float-pair state u/ulo, and return the next
+// stage's input.  The large term E u is formed once per step, at the last
+// stage (u is unchanged until then), from E and u both held as float pairs;
+// the four O(h) terms f1 N(u) + f2x2 N(a) + f2x2 N(b) + f3 N(c) are summed in
+// FP32 and added to it in float-pair arithmetic.  Shared by the
+// register-resident sweep and the lock-step DFT-GEMM sweep so both apply the
+// same arithmetic.
 __device__ __forceinline__ cf etd32_stage(int stage, int i, cf bn, cf& u, cf& ulo, cf& nu, cf& a1, cf& acc,
-                                          cf& acclo, const EtdView<float>& e, const cf* __restrict__ E_lo) {
+                                          const EtdView<float>& e, const cf* __restrict__ E_lo) {
   if (stage == 0) {
     nu = bn;
+    acc = ldgc(e.f1 + i) * bn;
     a1 = ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn;
-    const cdf s = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(E_lo + i), u, ulo), ldgc(e.f1 + i) * bn);
-    acc = mk<float>(s.re.hi, s.im.hi);
-    acclo = mk<float>(s.re.lo, s.im.lo);
     return a1;
   } else if (stage == 3) {
-    const cf t = ldgc(e.f3 + i) * bn;
-    const df re = df_add_f(df{acc.x, acclo.x}, t.x);
-    const df im = df_add_f(df{acc.y, acclo.y}, t.y);
-    u = mk<float>(re.hi, im.hi);
-    ulo = mk<float>(re.lo, im.lo);
+    const cdf s = cdf_add(cdf_mul(ldgc(e.E + i), ldgc(E_lo + i), u, ulo), acc + ldgc(e.f3 + i) * bn);
+    u = mk<float>(s.re.hi, s.im.hi);
+    ulo = mk<float>(s.re.lo, s.im.lo);
     return u;
   } else {
-    const cf t = ldgc(e.f2x2 + i) * bn;
-    const df re = df_add_f(df{acc.x, acclo.x}, t.x);
-    const df im = df_add_f(df{acc.y, acclo.y}, t.y);
-    acc = mk<float>(re.hi, im.hi);
-    acclo = mk<float>(re.lo, im.lo);
+    acc = acc + ldgc(e.f2x2 + i) * bn;
     return (stage == 1) ? ldgc(e.E2 + i) * u + ldgc(e.Q + i) * bn
                         : ldgc(e.E2 + i) * a1 + ldgc(e.Q + i) * (2.0f * bn - nu);
   }
@@ -351,7 +340,8 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
       pack_mode<T, N>(Z0, Z1, k, u[r], is, ss);
     }
   }
-  for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+  for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK)
+    if (k > K) zero_mode<T, N>(Z0, Z1, k);
   __syncthreads();
 
   const EtdView<T> e = tb.etd;
@@ -398,14 +388,15 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
               nx[q] = (stage == 1) ? E2 * u[r][q] + (0.5f * h) * bn[q] : ldgc(e.E + i) * u[r][q] + h * w;
             }
           } else {
-            nx[q] = etd32_stage(stage, i, bn[q], u[r][q], ulo[r][q], nu[r][q], a1[r][q], acc[r][q], acclo[r][q], e,
-                                tb.E_lo);
+            nx[q] = etd32_stage(stage, i, bn[q], u[r][q], ulo[r][q], nu[r][q], a1[r][q], acc[r][q], e, tb.E_lo);
           }
         }
         if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
       }
       if (pack_next)
-        for (int k = K1 + threadIdx.x; k <= zero_end<N>(); k += BLOCK) zero_mode<T, N>(Z0, Z1, k);
+        // bins above the kept modes, cleared by the threads whose own wavenumber lies there
+        for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK)
+          if (k > K) zero_mode<T, N>(Z0, Z1, k);
       __syncthreads();
     }
   }
