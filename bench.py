@@ -43,7 +43,7 @@ FP64_ALU_PEAK_TFLOPS = 1.25
 CPU_SAMPLE_SLICES = 64          # cpu_baseline sample (about 10 s of oracle work)
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fine-sweep kernel on this workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
-FINE_TRAFFIC_BYTES = {"fp32": 2259456, "fp64": None}
+FINE_TRAFFIC_BYTES = {"fp32": 2256896, "fp64": None}
 REFERENCE_SAMPLE_SLICES = 8     # per-step sample of the reference arm
 
 
