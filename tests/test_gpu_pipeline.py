@@ -143,3 +143,19 @@ def test_pipeline_option_rules():
             assert ei.value.status == b.ARP_EINVAL
         with pytest.raises(b.ArpError):
             b.arp_parareal_solve(s.ctx)  # no initial state
+
+
+@pytest.mark.parametrize("n,S,chunk", [(8, 1, 1), (8, 2, 1), (16, 3, 2), (32, 5, 4), (64, 9, 4)])
+def test_pipeline_smallest_problems(n, S, chunk):
+    # the smallest grids (no outer FFT stage at N = 8), one to nine slices,
+    # chunks of one or more links with a ragged last chunk
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    p = o.Params(n, 0.05, 1e-3, 0.1, 0.02, 4)
+    u0 = ri.random_spectrum(n, o.kept_modes(n), 4.0, 3) * n
+    kmax = min(3, S + 1)
+    got = _solve(b, p, u0, S, b.ARP_FP32, chunk if chunk >= 2 else 1, kmax)
+    assert got[3]["pipelined"] == 1
+    _same(got, _solve(b, p, u0, S, b.ARP_FP32, 0, kmax))
+    ref = o.parareal(u0, p, S, kmax)
+    assert per_state_rel_l2(got[0][1:], ref.iterates[kmax][1:]).max() <= 1e-5
