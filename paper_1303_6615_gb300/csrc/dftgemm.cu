@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(32 * kAvgChunks) dft_unpack_avg_kernel(
 }
 
 // Per (slice, k): unpack N of the stage and apply the ETDRK4 combination of
-// that stage (the formulas of the FP32 fine sweep, float-pair state and update
-// sum), writing the next stage's input XS.
+// that stage (the formulas of the FP32 fine sweep: float-pair state, FP32 sum
+// of the stage terms), writing the next stage's input XS.
 __global__ void dft_fine_stage_kernel(const float* __restrict__ Q, int S_, int K, int R, int stage,
                                       FineTabs<float> tb, cf* U, cf* ULO, cf* NU, cf* A1, cf* ACC,
                                       cf* XS) {

@@ -8,8 +8,9 @@
 //     u+ = E u + f1 N(u) + 2 f2 (N(a1) + N(a2)) + f3 N(a3).
 //
 // One CUDA block per state.  The state's mode arrays (u, N(u), a1 and the
-// running sum of the update) and the two FFT lanes stay in shared memory for
-// the whole sweep; only the input and output states touch global memory.
+// running sum of the update) and the two FFT lanes stay on chip (shared
+// memory, or registers in the FP32 register-resident sweep) for the whole
+// sweep; only the input and output states touch global memory.
 // After each transform a single pass over wavenumbers unpacks N, applies the
 // ETDRK4 combination for the stage, and packs the next stage's input.
 //
@@ -19,10 +20,12 @@
 //     u+ = E u + h/6 (E N(u) + 2 E2 (N(x2) + N(x3)) + N(x4)).
 //
 // FP32 path: transforms, products, stage values a1..a3 and the N(.) terms are
-// FP32, but the state u and the running update sum are carried as float pairs
-// hi + lo and multiplied by E = e^{h lambda} held as a float pair too, so the
-// exact linear propagation (a pure phase and decay per mode) does not pick up
-// a rounding error every step.  Only the N-evaluation input uses u_hi.
+// FP32, but the state u is carried as a float pair hi + lo and multiplied by
+// E = e^{h lambda} held as a float pair too, so the exact linear propagation
+// (a pure phase and decay per mode) does not pick up a rounding error every
+// step.  For ETDRK4 the four O(h) terms of the update are summed in FP32 and
+// added to the float-pair E u once per step; integrating-factor RK4 keeps its
+// update sum as a float pair.  Only the N-evaluation input uses u_hi.
 #pragma once
 
 #include <type_traits>
@@ -74,7 +77,7 @@ constexpr int fine_mode_arrays() {
   return std::is_same<T, float>::value ? 5 : 4;  // u, N(u), a1, acc (+ u_lo)
 }
 
-// Shared memory of one state's transform: two padded lanes and the twiddle tables.
+// Shared memory of one state's transform: two lanes and the twiddle tables.
 template <typename T>
 constexpr int lanes_and_twiddles(int logn) {
   return 2 * padded_len<T>(1 << logn) + twiddle_count(logn);
@@ -267,8 +270,9 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
 
 // FP32 fine sweep with the ETDRK4 state in registers: thread t owns the
 // wavenumbers k = t + r BLOCK (r < MPT), holding u (float pair), N(u), a1 and
-// the update sum (float pair) for the three branches; shared memory holds only
-// the two FFT lanes, the twiddle tables and the eigenvector constants.
+// the update sum (FP32 for ETDRK4, a float pair for integrating-factor RK4) for
+// the three branches; shared memory holds only the two FFT lanes, the twiddle
+// tables and the eigenvector constants.
 template <int LOGN, int BLOCK>
 struct F32Layout {
   static constexpr int K1 = ((1 << LOGN) - 1) / 3 + 1;

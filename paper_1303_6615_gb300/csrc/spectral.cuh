@@ -18,10 +18,12 @@
 //           spectrum out.
 // The stage spans are N, N/8, ... down to a middle span of 8, 4 or 2 (the
 // remainder of log2 N by 3); each outer stage is one shared-memory round trip
-// of radix-8 butterflies held in registers.  Lane arrays are stored padded
-// (one slot every 16 float or 8 double elements) so that every stage's
-// accesses are free of bank conflicts, and each outer stage reads its twiddles
-// W_L^{qj}, q = 1..7, from its own table laid out q-major (consecutive j).
+// of radix-8 butterflies held in registers.  Lane arrays are laid out so that
+// the stages' accesses avoid bank conflicts (FP32 lanes of 128 points or more
+// XOR-swizzled, the others padded with one slot every 16 float or 8 double
+// elements; see pidx), and each outer stage reads its twiddles W_L^{qj},
+// q = 1..7, from its own table laid out q-major (consecutive j).  The span-N
+// stages skip the bins 3N/8 .. 5N/8-1, which the 2/3 rule keeps zero.
 //   unpack  per k <= K: P1 = (Z0_k + conj Z0_{-k})/2, P2 = (Z0_k - conj Z0_{-k})/(2i),
 //           P3 = Z1_k; N_k = (P1, P2, i k P3)/N; b_k = R_k^H N_k.
 //
