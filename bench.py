@@ -748,7 +748,8 @@ def run_precision(args) -> dict:
     M=128): per-field relative L2 error of one fine sweep in FP32 bulk, 3xTF32 and
     2xBF16 DFT-GEMMs against the FP64 path (which the GPU tests hold to the FP64
     oracle within 1e-10) and the mean-height drift of each; then full-size parareal,
-    FP32 against FP64 (iterates k = 0..3) and the time per iteration of each."""
+    FP32 against FP64 (iterates k = 0..3) and the time per iteration of each, and the
+    FP32 solve of the same levels level by level and pipelined."""
     import numpy as np
     import torch
 
@@ -790,6 +791,27 @@ def run_precision(args) -> dict:
                 its.append(U.cpu().numpy())
             iterates[name] = its
             out["parareal_fp32_vs_fp64"][name + "_ms_per_iteration"] = ms[1:]
+            if prec == b.ARP_FP32:
+                # the same three iterations as one solve, level by level and pipelined
+                b.arp_set_option(s.ctx, b.ARP_OPT_KMAX, 3)
+                solve = {}
+                for label, pipe in (("level_by_level", 0), ("pipelined", 1)):
+                    b.arp_set_option(s.ctx, b.ARP_OPT_PIPELINE, pipe)
+                    b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+                    b.arp_parareal_solve(s.ctx)  # warm-up
+                    ts = []
+                    for _ in range(2):
+                        b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        b.arp_parareal_solve(s.ctx)
+                        torch.cuda.synchronize()
+                        ts.append(1e3 * (time.perf_counter() - t0))
+                    solve[label + "_ms"] = min(ts)
+                    solve[label + "_ran_pipelined"] = bool(b.arp_pipeline_info(s.ctx)["pipelined"])
+                    b.arp_get_slices(s.ctx, U)
+                    solve[label + "_equals_iterates"] = bool(np.array_equal(U.cpu().numpy(), its[3]))
+                out["parareal_fp32_vs_fp64"]["fp32_solve_predictor_plus_3"] = solve
     d = []
     for k in range(4):
         a, r = iterates["fp32"][k][1:], iterates["fp64"][k][1:]
