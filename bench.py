@@ -909,7 +909,8 @@ def serve_requests(count: int, seed: int):
 
 def run_serve(args) -> dict:
     """Poisson request streams (rates 10, 100, 1000 per second, 64 requests each)
-    through the continuous-batching FP32 server, against the plain FP64 path
+    through the continuous-batching FP32 server (with and without the one-call
+    solve of a request that runs alone), against the plain FP64 path
     serving the same requests one at a time in arrival order (first come first
     served, each request's FP64 service time measured on its own)."""
     import numpy as np
@@ -933,15 +934,19 @@ def run_serve(args) -> dict:
     for rate in (10.0, 100.0, 1000.0):
         rng = np.random.default_rng(int(rate))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
-        reqs = serve_requests(count, 3000)
-        server = serve.Server(memory_budget=24 << 30, max_active=256, precision=b.ARP_FP32)
-        try:
-            t0 = server.clock()
-            done = serve.replay(server, list(zip(arrivals.tolist(), reqs)))
-            makespan = server.clock() - t0
-        finally:
-            server.close()
-        lat = np.array([r.latency for r in done])
+        stats = {}
+        for lone in (True, False):
+            reqs = serve_requests(count, 3000)
+            server = serve.Server(memory_budget=24 << 30, max_active=256, precision=b.ARP_FP32, lone_solve=lone)
+            try:
+                t0 = server.clock()
+                done = serve.replay(server, list(zip(arrivals.tolist(), reqs)))
+                makespan = server.clock() - t0
+            finally:
+                server.close()
+            lat = np.array([r.latency for r in done])
+            stats[lone] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                           "throughput_req_s": count / makespan}
         # first come first served, one at a time, FP64
         finish, lat64 = 0.0, []
         for a, s in zip(arrivals, service64):
@@ -949,8 +954,8 @@ def run_serve(args) -> dict:
             lat64.append(finish - a)
         lat64 = np.array(lat64)
         out["rates"][str(int(rate))] = {
-            "batched_fp32": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                             "throughput_req_s": count / makespan},
+            "batched_fp32": stats[True],
+            "batched_fp32_levels_only": stats[False],
             "fp64_one_at_a_time": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
                                    "throughput_req_s": count / (finish - 0.0)},
         }

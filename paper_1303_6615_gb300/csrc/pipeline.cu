@@ -24,6 +24,8 @@
 #include <cuda.h>
 
 #include <cmath>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -34,10 +36,24 @@
 
 namespace arp {
 
+// The device's SM partition, made once per process and shared by every
+// context: green context 0 holds the chain's cluster, 1 the rest for the fine
+// sweeps.  A green context may be current on one thread at a time, so pushing
+// either one holds `mu`.
+struct Partition {
+  bool ok = false;
+  std::string why;
+  CUgreenCtx g[2] = {nullptr, nullptr};
+  CUcontext x[2] = {nullptr, nullptr};
+  int sms[2] = {0, 0};
+  std::mutex mu;
+};
+
 struct Pipe {
   bool built = false, ok = false;
   std::string why;                    // why the pipeline is unavailable
-  CUgreenCtx g[2] = {nullptr, nullptr};  // 0: chain partition, 1: fine partition
+  Partition* part = nullptr;          // the shared partition (not owned)
+  CUgreenCtx g[2] = {nullptr, nullptr};  // its green contexts: 0 chain, 1 fine
   CUcontext x[2] = {nullptr, nullptr};
   int sms[2] = {0, 0};
   int cluster = 0;                    // chain cluster size that fits the chain partition
@@ -104,11 +120,14 @@ const Driver& driver() {
   return d;
 }
 
-// Makes a partition's context current for the enclosed runtime calls.
+// Makes a partition's context current for the enclosed runtime calls (the
+// partition's lock held meanwhile).
 struct Current {
   const Driver& d;
+  std::lock_guard<std::mutex> lock;
   bool pushed;
-  Current(const Driver& drv, CUcontext x) : d(drv), pushed(drv.push(x) == CUDA_SUCCESS) {}
+  Current(const Driver& drv, Partition* part, CUcontext x)
+      : d(drv), lock(part->mu), pushed(drv.push(x) == CUDA_SUCCESS) {}
   ~Current() {
     CUcontext prev;
     if (pushed) d.pop(&prev);
@@ -120,7 +139,8 @@ arp_status drv_check(arp_ctx* c, CUresult e, const char* what) {
   return fail(c, ARP_ECUDA, std::string("pipeline: ") + what + " failed (CUresult " + std::to_string((int)e) + ")");
 }
 
-void destroy_partition(Pipe& p) {
+// The per-context streams and events (the shared partition stays).
+void destroy_streams(Pipe& p) {
   const Driver& d = driver();
   if (!d.ok) return;
   for (CUevent& e : p.ec) if (e) d.eventDestroy(e);
@@ -134,43 +154,58 @@ void destroy_partition(Pipe& p) {
   if (p.sc) d.streamDestroy(p.sc);
   p.done = p.start = nullptr;
   p.sc = nullptr;
-  for (int i = 0; i < 2; ++i) {
-    if (p.g[i]) d.greenDestroy(p.g[i]);
-    p.g[i] = nullptr;
-    p.x[i] = nullptr;
-    p.sms[i] = 0;
-  }
 }
 
-// Splits the device's SMs: a group of at least `min_chain` SMs (grouped so
-// that large clusters fit) and the rest.  False, with p.why set, if the split
-// or the contexts cannot be made.
-bool make_partition(Pipe& p, int device, unsigned min_chain) {
+// Splits the device's SMs into a group of at least 16 SMs, grouped so that
+// large clusters fit (the chain's), and the rest.  part.ok false, with
+// part.why set, if the split or the contexts cannot be made.
+void make_partition(Partition& part, int device) {
   const Driver& d = driver();
   CUdevResource all{}, grp{}, rest{};
+  if (!d.ok) {
+    part.why = "the driver has no green-context entry points";
+    return;
+  }
   if (d.getDevResource((CUdevice)device, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS) {
-    p.why = "the device's SM resource cannot be read";
-    return false;
+    part.why = "the device's SM resource cannot be read";
+    return;
   }
   unsigned nb = 1;
-  if (d.split(&grp, &nb, &all, &rest, CU_DEV_SM_RESOURCE_SPLIT_MAX_POTENTIAL_CLUSTER_SIZE, min_chain) !=
-          CUDA_SUCCESS ||
+  if (d.split(&grp, &nb, &all, &rest, CU_DEV_SM_RESOURCE_SPLIT_MAX_POTENTIAL_CLUSTER_SIZE, 16) != CUDA_SUCCESS ||
       nb < 1 || rest.sm.smCount < 1) {
-    p.why = "the SMs cannot be split into a chain group and a fine group";
-    return false;
+    part.why = "the SMs cannot be split into a chain group and a fine group";
+    return;
   }
   CUdevResource* parts[2] = {&grp, &rest};
   for (int i = 0; i < 2; ++i) {
     CUdevResourceDesc desc;
     if (d.genDesc(&desc, parts[i], 1) != CUDA_SUCCESS ||
-        d.greenCreate(&p.g[i], desc, (CUdevice)device, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS ||
-        d.fromGreen(&p.x[i], p.g[i]) != CUDA_SUCCESS) {
-      p.why = "a green context cannot be created";
-      return false;
+        d.greenCreate(&part.g[i], desc, (CUdevice)device, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS ||
+        d.fromGreen(&part.x[i], part.g[i]) != CUDA_SUCCESS) {
+      part.why = "a green context cannot be created";
+      for (int j = 0; j <= i; ++j)
+        if (part.g[j]) d.greenDestroy(part.g[j]);
+      part.g[0] = part.g[1] = nullptr;
+      part.x[0] = part.x[1] = nullptr;
+      return;
     }
-    p.sms[i] = (int)parts[i]->sm.smCount;
+    part.sms[i] = (int)parts[i]->sm.smCount;
   }
-  return true;
+  part.ok = true;
+}
+
+// The partition of `device`, made on the first request of the process; it
+// lives as long as the process.
+Partition* shared_partition(int device) {
+  static std::mutex mu;
+  static std::map<int, std::unique_ptr<Partition>> parts;
+  std::lock_guard<std::mutex> lock(mu);
+  std::unique_ptr<Partition>& part = parts[device];
+  if (!part) {
+    part.reset(new Partition);
+    make_partition(*part, device);
+  }
+  return part.get();
 }
 
 // Per-chunk streams (fine partition) and events for chunks of `chunk` links.
@@ -189,11 +224,11 @@ arp_status make_chunks(arp_ctx* c, Pipe& p, int chunk) {
     CUevent e0 = nullptr, e1 = nullptr;
     CUstream s1 = nullptr;
     {
-      Current cur(d, p.x[0]);
+      Current cur(d, p.part, p.x[0]);
       if ((r = drv_check(c, d.eventCreate(&e0, CU_EVENT_DISABLE_TIMING), "event")) != ARP_OK) return r;
     }
     p.ec.push_back(e0);
-    Current cur(d, p.x[1]);
+    Current cur(d, p.part, p.x[1]);
     if ((r = drv_check(c, d.greenStream(&s1, p.g[1], CU_STREAM_NON_BLOCKING, 0), "fine stream")) != ARP_OK)
       return r;
     p.sf.push_back(s1);
@@ -203,36 +238,37 @@ arp_status make_chunks(arp_ctx* c, Pipe& p, int chunk) {
   return ARP_OK;
 }
 
-// The partition (the smallest chain group on which a cluster of 16 fits,
-// else one of 8), the chain stream, events and buffers.  ARP_OK with nothing
-// made (p.why set) where the driver or the device cannot provide them.
+// c's streams, events and buffers on the shared partition, after checking
+// that c's chain cluster (16 CTAs, else 8) fits the chain partition.  ARP_OK
+// with nothing made (p.why set) where the partition is unavailable or the
+// cluster does not fit.
 arp_status make_pipe(arp_ctx* c, Pipe& p) {
   const Driver& d = driver();
-  if (!d.ok) {
-    p.why = "the driver has no green-context entry points";
+  Partition* part = shared_partition(c->device);
+  if (!part->ok) {
+    p.why = part->why;
     return ARP_OK;
   }
-  bool found = false;
+  p.part = part;
+  for (int i = 0; i < 2; ++i) {
+    p.g[i] = part->g[i];
+    p.x[i] = part->x[i];
+    p.sms[i] = part->sms[i];
+  }
   for (int want : {16, 8}) {
-    for (unsigned m : {16u, 20u, 24u, 32u}) {
-      destroy_partition(p);
-      if (!make_partition(p, c->device, m)) continue;
-      Current cur(d, p.x[0]);
-      ChainRange probe;
-      probe.check_only = true;
-      probe.cluster = want;
-      if (launch_cluster_chain(c, c->U, c->Ge, nullptr, nullptr, &probe) == ARP_OK) {
-        p.cluster = want;
-        found = true;
-        break;
-      }
+    Current cur(d, p.part, p.x[0]);
+    ChainRange probe;
+    probe.check_only = true;
+    probe.cluster = want;
+    if (launch_cluster_chain(c, c->U, c->Ge, nullptr, nullptr, &probe) == ARP_OK) {
+      p.cluster = want;
+      break;
     }
-    if (found) break;
   }
   c->err.clear();
-  if (!found) {
-    destroy_partition(p);
-    if (p.why.empty()) p.why = "no chain cluster fits a partition of the SMs";
+  if (!p.cluster) {
+    p.why = "no chain cluster fits the chain partition";
+    p.part = nullptr;
     return ARP_OK;
   }
   arp_status r;
@@ -242,7 +278,7 @@ arp_status make_pipe(arp_ctx* c, Pipe& p) {
       (r = check_cuda(c, cudaMallocHost(&p.hchg, sizeof(double)), "pipeline: change read-back")) != ARP_OK ||
       (r = drv_check(c, d.eventCreate(&p.start, CU_EVENT_DISABLE_TIMING), "event")) != ARP_OK)
     return r;
-  Current cur(d, p.x[0]);
+  Current cur(d, p.part, p.x[0]);
   if ((r = drv_check(c, d.greenStream(&p.sc, p.g[0], CU_STREAM_NON_BLOCKING, 0), "chain stream")) != ARP_OK ||
       (r = drv_check(c, d.eventCreate(&p.done, CU_EVENT_DISABLE_TIMING), "event")) != ARP_OK)
     return r;
@@ -342,16 +378,16 @@ arp_status level(arp_ctx* c, Pipe& p, const Level& lv, int L, bool chain, bool f
   arp_status r;
   for (int j = 0; j < p.nchunks; ++j) {
     if (chain) {
-      Current cur(d, p.x[0]);
+      Current cur(d, p.part, p.x[0]);
       if ((r = chain_chunk(c, p, lv, L, j)) != ARP_OK) return r;
     }
     if (fine) {
-      Current cur(d, p.x[1]);
+      Current cur(d, p.part, p.x[1]);
       if ((r = fine_chunk(c, p, lv, L, j, chain)) != ARP_OK) return r;
     }
   }
   if (!chain) return ARP_OK;
-  Current cur(d, p.x[0]);
+  Current cur(d, p.part, p.x[0]);
   if (L >= 1) {
     max_kernel<<<1, 256, 0, (cudaStream_t)p.sc>>>(c->rel, c->slices, c->scalar);
     if ((r = check_cuda(c, cudaGetLastError(), "pipeline: norm")) != ARP_OK) return r;
@@ -389,14 +425,14 @@ arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, in
   // order after the caller's stream; u0 into both buffers
   if ((r = drv_check(c, d.eventRecord(p.start, (CUstream)user), "record")) != ARP_OK) return r;
   {
-    Current cur(d, p.x[0]);
+    Current cur(d, p.part, p.x[0]);
     if ((r = drv_check(c, d.waitEvent(p.sc, p.start, 0), "wait")) != ARP_OK) return r;
     if ((r = check_cuda(c, cudaMemcpyAsync(c->Uold, c->U, st * sizeof(cd), cudaMemcpyDeviceToDevice,
                                            (cudaStream_t)p.sc), "pipeline: copy u0")) != ARP_OK)
       return r;
   }
   {
-    Current cur(d, p.x[1]);
+    Current cur(d, p.part, p.x[1]);
     for (CUstream s : p.sf)
       if ((r = drv_check(c, d.waitEvent(s, p.start, 0), "wait")) != ARP_OK) return r;
   }
@@ -405,7 +441,7 @@ arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, in
   auto join = [&]() {
     arp_status q;
     {
-      Current cur(d, p.x[0]);
+      Current cur(d, p.part, p.x[0]);
       q = drv_check(c, d.eventRecord(p.done, p.sc), "record");
     }
     if (q == ARP_OK) q = drv_check(c, d.waitEvent((CUstream)user, p.done, 0), "wait");
@@ -455,7 +491,7 @@ void pipeline_release(arp_ctx* c) {
   Pipe& p = *c->pipe;
   if (p.sc) cudaStreamSynchronize((cudaStream_t)p.sc);
   for (CUstream s : p.sf) cudaStreamSynchronize((cudaStream_t)s);
-  destroy_partition(p);
+  destroy_streams(p);
   if (p.Fb2) cudaFree(p.Fb2);
   if (p.Wc) cudaFree(p.Wc);
   if (p.hchg) cudaFreeHost(p.hchg);

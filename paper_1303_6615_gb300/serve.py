@@ -5,7 +5,9 @@ dt, quadrature points M, initial spectrum u0) solved until KMAX iterations or a
 relative change <= TOL.  The server keeps every admitted problem's slice states
 resident on the device and advances all of them together: each `step()` runs
 one batched parareal level (arp_batch_iterate), so the fine sweeps and coarse
-chains of all active problems share fused launches.  Requests that arrive while
+chains of all active problems share fused launches.  A request that runs alone
+with nothing queued is finished in one arp_parareal_solve instead (its levels
+overlapped where the library pipelines them), with the same result.  Requests that arrive while
 others are running are admitted at the next step, in arrival order, as slots
 and device memory (arp_query_bytes) free up; finished problems leave the batch
 and their slices are copied to the host.
@@ -53,7 +55,7 @@ class Server:
     ones by one parareal level per step."""
 
     def __init__(self, memory_budget: int = 16 << 30, max_active: int = 256, precision: int = b.ARP_FP32,
-                 stream=None):
+                 stream=None, lone_solve: bool = True):
         import torch
         self.torch = torch
         self.budget = memory_budget
@@ -68,6 +70,10 @@ class Server:
         self.members: list[int] = []
         self.t0 = time.perf_counter()
         self.next_id = 0
+        # a request running alone with nothing queued finishes in one arp_parareal_solve
+        # (its levels pipelined where the library can), which gives the same slices,
+        # levels and change as the batched levels
+        self.lone_solve = lone_solve
 
     def clock(self) -> float:
         return time.perf_counter() - self.t0
@@ -110,8 +116,15 @@ class Server:
         self._admit()
         if not self.active:
             return 0
-        self._sync_members()
-        levels, changes = b.arp_batch_iterate(self.batch, len(self.active), self.stream)
+        if self.lone_solve and len(self.active) == 1 and not self.pending:
+            r, s = self.active[0]
+            b.arp_set_option(s.ctx, b.ARP_OPT_KMAX, r.k_max)
+            b.arp_set_option(s.ctx, b.ARP_OPT_TOL, r.tol)
+            lv, ch = b.arp_parareal_solve(s.ctx, self.stream)
+            levels, changes = [lv], [ch]
+        else:
+            self._sync_members()
+            levels, changes = b.arp_batch_iterate(self.batch, len(self.active), self.stream)
         still = []
         for (r, s), lv, ch in zip(self.active, levels, changes):
             r.levels, r.change = lv, ch

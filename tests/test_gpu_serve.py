@@ -28,8 +28,9 @@ def test_served_results_equal_solo_results(precision):
     from paper_1303_6615_gb300 import serve
     reqs = _requests(serve)
     biggest = max(b.arp_query_bytes(r.n_grid, r.slices, r.m_quad, precision) for r in reqs)
-    # at most 3 requests in flight, and memory for about 2.5 of the largest
-    server = serve.Server(memory_budget=int(2.5 * biggest), max_active=3, precision=precision)
+    # at most 3 requests in flight, and memory for about 2.5 of the largest; every
+    # step one batched level (a lone request's one-call solve has its own test)
+    server = serve.Server(memory_budget=int(2.5 * biggest), max_active=3, precision=precision, lone_solve=False)
     try:
         trace = [(0.002 * i, r) for i, r in enumerate(reqs)]
         done = serve.replay(server, trace)
@@ -43,3 +44,38 @@ def test_served_results_equal_solo_results(precision):
         assert r.latency >= 0 and r.levels <= r.k_max
         alone = serve.solve_alone(r, precision)
         np.testing.assert_array_equal(r.result, alone)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_lone_request_solve_equals_batched_levels(precision):
+    # requests spaced out so that each runs alone for part of its life: finishing a
+    # lone request in one arp_parareal_solve (pipelined where it applies) gives the
+    # slices, level and change of the batched levels
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import serve
+    got = {}
+    for lone in (True, False):
+        reqs = _requests(serve)[:4]
+        server = serve.Server(memory_budget=1 << 30, max_active=4, precision=precision, lone_solve=lone)
+        try:
+            done = serve.replay(server, [(0.03 * i, r) for i, r in enumerate(reqs)])
+        finally:
+            server.close()
+        got[lone] = {r.rid: r for r in done}
+    assert sorted(got[True]) == sorted(got[False]) == list(range(4))
+    for rid, r in got[True].items():
+        q = got[False][rid]
+        assert (r.levels, r.change) == (q.levels, q.change)
+        np.testing.assert_array_equal(r.result, q.result)
+        np.testing.assert_array_equal(r.result, serve.solve_alone(r, precision))
+    # one request alone from the start: served by the one-call solve
+    r = _requests(serve)[2]
+    server = serve.Server(memory_budget=1 << 30, max_active=4, precision=precision)
+    try:
+        server.submit(r)
+        server.step()
+        assert not server.active and server.done == [r]
+        assert r.levels == r.k_max or r.change <= r.tol
+    finally:
+        server.close()
+    np.testing.assert_array_equal(r.result, serve.solve_alone(r, precision))
