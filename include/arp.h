@@ -287,6 +287,14 @@ const char* arp_batch_last_error(const arp_batch* batch);
  * predictor), out[7]=precision. */
 arp_status arp_info(const arp_ctx* ctx, int* out8);
 
+/* arp_alu_peak: the measured plain-ALU peak of the current device: fused
+ * multiply-adds of `precision` (ARP_FP32 or ARP_FP64) in independent register
+ * chains on every SM, timed with events on `stream` (which it synchronises);
+ * *tflops counts 2 flops per FMA.  A measurement aid for roofline fractions.
+ * ARP_EINVAL for another precision or a NULL pointer; ARP_ECUDA or ARP_ENOMEM
+ * on a CUDA failure. */
+arp_status arp_alu_peak(int precision, double* tflops, void* stream);
+
 /* arp_pipeline_info: how the last arp_parareal_solve ran: out[0] = 1 if
  * pipelined (ARP_OPT_PIPELINE), else 0; out[1], out[2] = SMs of the chain and
  * fine partitions, out[3] = links per chunk, out[4] = CTAs of the chain's

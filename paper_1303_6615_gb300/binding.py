@@ -50,6 +50,7 @@ _SIGS = {
     "arp_last_error": (ctypes.c_char_p, [_P]),
     "arp_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "arp_pipeline_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "arp_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "arp_coarse_avg_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P,
                                              _P, ctypes.c_int, _P]),
     "arp_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
@@ -128,6 +129,15 @@ def arp_info(ctx: int) -> dict:
     _check(ctx, load_library().arp_info(ctx, out))
     keys = ("N", "H", "K", "slices", "M", "steps", "level", "precision")
     return dict(zip(keys, list(out)))
+
+
+def arp_alu_peak(precision: int, stream=None) -> float:
+    """Measured plain-ALU peak (TFLOP/s) of the current device for ARP_FP32 or ARP_FP64."""
+    t = ctypes.c_double(0.0)
+    st = load_library().arp_alu_peak(precision, ctypes.byref(t), _stream(stream))
+    if st != ARP_OK:
+        raise ArpError(st, "arp_alu_peak failed")
+    return t.value
 
 
 def arp_pipeline_info(ctx: int) -> dict:

@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libarp.so")
 
 SOURCES = ["api.cu", "tables.cu", "fine64.cu", "fine32.cu", "chain64.cu", "chain32.cu", "coarse.cu", "strang64.cu",
            "strang32.cu", "ifrk64.cu", "ifrk32.cu", "dftgemm.cu",
-           "parareal.cu", "pipeline.cu", "static_avg.cu",
+           "parareal.cu", "pipeline.cu", "peaks.cu", "static_avg.cu",
            "batch.cu", "batch64.cu", "batch32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

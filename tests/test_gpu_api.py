@@ -104,3 +104,16 @@ def test_smallest_problems(n, m, slices):
                 its.append(to_host(U))
         for k in range(3):
             assert per_state_rel_l2(its[k][1:], ref.iterates[k][1:]).max() <= tol, (prec, k)
+
+
+def test_alu_peak_probe():
+    # the measured FMA peak the bench reports beside the nominal one: positive, of
+    # the right order for the part (FP32 far above FP64), other precisions refused
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    f32 = b.arp_alu_peak(b.ARP_FP32)
+    f64 = b.arp_alu_peak(b.ARP_FP64)
+    assert 10.0 < f32 < 200.0 and 0.1 < f64 < 10.0 and f32 > 8 * f64
+    with pytest.raises(b.ArpError) as ei:
+        b.arp_alu_peak(b.ARP_TF32X3)
+    assert ei.value.status == b.ARP_EINVAL
