@@ -159,3 +159,15 @@ def test_pipeline_smallest_problems(n, S, chunk):
     _same(got, _solve(b, p, u0, S, b.ARP_FP32, 0, kmax))
     ref = o.parareal(u0, p, S, kmax)
     assert per_state_rel_l2(got[0][1:], ref.iterates[kmax][1:]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("scheme", [1, 2], ids=["strang", "ifrk4"])
+def test_pipelined_solve_with_other_fine_schemes(scheme):
+    # the chunked fine launches run whichever fine scheme the context uses
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    p, u0, S = _params(n=64, S=12, m=16)
+    opts = ((b.ARP_OPT_FINE_SCHEME, scheme),)
+    got = _solve(b, p, u0, S, b.ARP_FP32, 4, 3, opts=opts)
+    assert got[3]["pipelined"] == 1
+    _same(got, _solve(b, p, u0, S, b.ARP_FP32, 0, 3, opts=opts))
