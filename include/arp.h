@@ -76,7 +76,8 @@ typedef enum {
   ARP_OPT_TOL = 5,         /* stopping tolerance of arp_parareal_solve (default 0) */
   ARP_OPT_CHAIN = 6,       /* serial coarse chain: 0 = automatic (one thread-block cluster,
                               else a cooperative grid with bounded grid barriers, else one
-                              launch per step; in FP64 the cooperative grid first), 1 =
+                              launch per step; in FP64 with M > 16 the cooperative grid
+                              first), 1 =
                               cooperative grid, 2 = launches, 3 = the cluster only; all give
                               the same result up to rounding (default 0) */
   ARP_OPT_FINE_BLOCK = 7,  /* FP32 fine sweep threads per slice: 0 = the default for the grid

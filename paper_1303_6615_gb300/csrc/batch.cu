@@ -275,8 +275,9 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
     std::vector<ClusterPlan> plans(g.second.size());
     arp_status pr = ARP_EINVAL;
     bool forced = false;
-    // a member whose chain would not run as a cluster on its own runs it on its own here too
-    // (FP64 in automatic mode prefers the cooperative grid), so batched = solo bit for bit
+    // a member whose chain might not run the batched cluster on its own runs it on its own
+    // here too (FP64 in automatic mode takes the cooperative grid above 16 nodes, and runs
+    // its own chain choice in any case), so batched = solo bit for bit
     for (int i : g.second) {
       const arp_ctx* c = b->ctx[i];
       forced |= (c->chain_mode == 1 || c->chain_mode == 2 || c->skip_arrival ||

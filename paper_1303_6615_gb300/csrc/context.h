@@ -136,6 +136,14 @@ arp_status launch_cluster_chain(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT, 
                                 const ChainRange* rg = nullptr);
 
 // parareal.cu
+// True where the automatic chain choice (ARP_OPT_CHAIN 0) takes the cooperative
+// grid before the cluster: FP64 with more than 16 quadrature nodes, where the
+// cluster's CTAs would each transform several nodes on the slow FP64 units
+// while the grid gives every node a block of its own.  With at most 16 nodes a
+// cluster CTA holds at most one node and the cluster's barriers are cheaper.
+inline bool fp64_grid_first(const arp_ctx* c) {
+  return c->chain_mode == 0 && c->precision == ARP_FP64 && c->M > 16;
+}
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);
 // The serial chain of one context (cluster, else cooperative grid, else launches).
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s);

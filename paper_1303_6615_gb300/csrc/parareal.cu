@@ -89,9 +89,10 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   }
   if (c->coarse_scheme == 1) return launch_strang_chain(c, c->U, c->Gc, V, s);
   r = ARP_EINVAL;
-  // In FP64 the chain's transforms are bound by GB300's FP64 throughput, so the
-  // cooperative grid (up to one node per SM) comes first; otherwise the cluster.
-  if (c->chain_mode == 0 && c->precision == ARP_FP64 && !c->skip_arrival) r = launch_chain(c, c->U, c->Gc, V, s);
+  // In FP64 with more than 16 nodes the chain's transforms are bound by GB300's
+  // FP64 throughput, so the cooperative grid (up to one node per SM) comes
+  // first; otherwise the cluster.
+  if (fp64_grid_first(c) && !c->skip_arrival) r = launch_chain(c, c->U, c->Gc, V, s);
   if (r != ARP_EINVAL) return r;
   if ((c->chain_mode == 0 || c->chain_mode == 3) && !c->skip_arrival) {
     r = launch_cluster_chain(c, c->U, c->Ge, V ? c->VT : nullptr, s);

@@ -403,7 +403,7 @@ arp_status level(arp_ctx* c, Pipe& p, const Level& lv, int L, bool chain, bool f
 bool pipeline_eligible(const arp_ctx* c) {
   if (c->pipeline == 0 || c->coarse_scheme != 0 || c->coarse_grid || dft_mode(c) || c->skip_arrival) return false;
   if (c->chain_mode == 3) return true;
-  return c->chain_mode == 0 && c->precision != ARP_FP64;
+  return c->chain_mode == 0 && !fp64_grid_first(c);
 }
 
 arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, int* k_done, double* change) {

@@ -116,16 +116,17 @@ def test_fp64_cluster_chain_pipelined():
     assert per_state_rel_l2(got[0][1:], ref.iterates[3][1:]).max() <= 1e-10
 
 
-@pytest.mark.parametrize("precision,opts", [
-    (1, (("ARP_OPT_CHAIN", 1),)),
-    (1, (("ARP_OPT_COARSE_SCHEME", 1),)),
-    (1, (("ARP_OPT_COARSE_GRID", 32),)),
-    (0, ()),
-], ids=["cooperative-chain", "strang-coarse", "coarse-grid", "fp64-auto-chain"])
-def test_out_of_scope_configurations_run_level_by_level(precision, opts):
+@pytest.mark.parametrize("precision,opts,m", [
+    (1, (("ARP_OPT_CHAIN", 1),), 16),
+    (1, (("ARP_OPT_COARSE_SCHEME", 1),), 16),
+    (1, (("ARP_OPT_COARSE_GRID", 32),), 16),
+    (0, (), 32),
+], ids=["cooperative-chain", "strang-coarse", "coarse-grid", "fp64-auto-chain-32-nodes"])
+def test_out_of_scope_configurations_run_level_by_level(precision, opts, m):
+    # (FP64 in automatic mode takes the cooperative grid above 16 nodes)
     cuda_or_skip()
     from paper_1303_6615_gb300 import binding as b
-    p, u0, S = _params(n=64, S=8, m=16)
+    p, u0, S = _params(n=64, S=8, m=m)
     o2 = tuple((getattr(b, k), v) for k, v in opts)
     got = _solve(b, p, u0, S, precision, 1, 2, opts=o2)
     assert got[3]["pipelined"] == 0
@@ -171,3 +172,15 @@ def test_pipelined_solve_with_other_fine_schemes(scheme):
     got = _solve(b, p, u0, S, b.ARP_FP32, 4, 3, opts=opts)
     assert got[3]["pipelined"] == 1
     _same(got, _solve(b, p, u0, S, b.ARP_FP32, 0, 3, opts=opts))
+
+
+def test_fp64_automatic_chain_with_few_nodes_is_pipelined():
+    # FP64 with at most 16 nodes chains in the cluster, so its solve is pipelined
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    p, u0, S = _params(n=64, S=12, m=10)
+    got = _solve(b, p, u0, S, b.ARP_FP64, 4, 3)
+    assert got[3]["pipelined"] == 1
+    _same(got, _solve(b, p, u0, S, b.ARP_FP64, 0, 3))
+    ref = o.parareal(u0, p, S, 3)
+    assert per_state_rel_l2(got[0][1:], ref.iterates[3][1:]).max() <= 1e-10
