@@ -537,13 +537,28 @@ def run_paper(args) -> dict:
                     times.append(e0.elapsed_time(e1) / 1e3)
                     b.arp_get_slices(s.ctx, U)
                     its.append(U.cpu().numpy())
-        return its, times
+            # the same levels as one arp_parareal_solve (pipelined where it applies)
+            b.arp_set_option(s.ctx, b.ARP_OPT_KMAX, kmax)
+            solve_s = []
+            for rep in range(2):
+                b.arp_set_initial(s.ctx, torch.from_numpy(u0).cuda())
+                e0, e1 = events()
+                e0.record()
+                b.arp_parareal_solve(s.ctx)
+                e1.record()
+                torch.cuda.synchronize()
+                solve_s.append(e0.elapsed_time(e1) / 1e3)
+            b.arp_get_slices(s.ctx, U)
+            same = bool(np.array_equal(U.cpu().numpy(), its[-1]))
+            solve = {"seconds": solve_s[-1], "pipelined": bool(b.arp_pipeline_info(s.ctx)["pipelined"]),
+                     "equals_iterates": same}
+        return its, times, solve
 
     out = {"mode": "paper", "precision": "fp64", "fine": "ETDRK4", "experiments": []}
     for e in ri.PAPER_EXPERIMENTS:
         u0 = ri.paper_initial_state(e.n_grid)
         ref, t_serial, steps = serial_fine(e, e.dT, e.slices, u0)
-        its, times = parareal(e, e.dT, e.slices, u0, 0, e.window)
+        its, times, solve = parareal(e, e.dT, e.slices, u0, 0, e.window)
         errs = [_linf_rel(U[1:], ref[1:], e.n_grid) for U in its]
         tau_f = t_serial / (e.slices * steps)          # one fine step of one slice
         tau_c = times[0] / e.slices                     # one link of the predictor's chain
@@ -555,11 +570,12 @@ def run_paper(args) -> dict:
         row["asymptotic"]["eq51_equal_costs"] = eq51_speedup(e.slices, steps, kmax)
         row["asymptotic"]["eq51_measured_costs"] = eq51_speedup(e.slices, steps, kmax, tau_f, tau_c)
         row["asymptotic"]["measured_speedup"] = t_serial / sum(times)
+        row["asymptotic"]["solve"] = dict(solve, measured_speedup=t_serial / solve["seconds"])
         row["standard"] = []
         for dT in e.standard_dT:
             S = int(round(e.t_end / dT))
             ref_s, t_ser_s, steps_s = serial_fine(e, dT, S, u0)
-            its_s, times_s = parareal(e, dT, S, u0, 1)
+            its_s, times_s, _ = parareal(e, dT, S, u0, 1)
             errs_s = [_linf_rel(U[1:], ref_s[1:], e.n_grid) for U in its_s]
             tc_s = times_s[0] / S
             tf_s = t_ser_s / (S * steps_s)
