@@ -184,3 +184,41 @@ def test_fp64_automatic_chain_with_few_nodes_is_pipelined():
     _same(got, _solve(b, p, u0, S, b.ARP_FP64, 0, 3))
     ref = o.parareal(u0, p, S, 3)
     assert per_state_rel_l2(got[0][1:], ref.iterates[3][1:]).max() <= 1e-10
+
+
+def test_concurrent_solves_on_two_threads():
+    # two host threads solve on their own contexts at once; the shared SM
+    # partition is pushed under its lock, and each thread's slices are the
+    # ones a sequential solve gives
+    import threading
+    torch = cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    cases = [_params(n=64, S=12, m=16), _params(n=128, S=16, m=16)]
+    seq = [_solve(b, p, u0, S, b.ARP_FP32, 1, 3)[0] for p, u0, S in cases]
+    out, errors = [None, None], []
+
+    def run(i):
+        try:
+            p, u0, S = cases[i]
+            dev = torch.device("cuda", 0)
+            torch.cuda.set_device(dev)
+            for _ in range(3):
+                with b.Solver(p.n_grid, p.eps, p.nu, S, p.dT, p.dt, p.m_quad, precision=b.ARP_FP32) as s:
+                    b.arp_set_option(s.ctx, b.ARP_OPT_KMAX, 3)
+                    b.arp_set_initial(s.ctx, to_dev(u0))
+                    b.arp_parareal_solve(s.ctx)
+                    U = torch.empty((S + 1, 3, p.H), dtype=torch.complex128, device="cuda")
+                    b.arp_get_slices(s.ctx, U)
+                    out[i] = to_host(U)
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=120)
+    assert not any(t.is_alive() for t in threads), "a solving thread did not finish"
+    assert not errors, errors
+    for i in range(2):
+        np.testing.assert_array_equal(out[i], seq[i])
