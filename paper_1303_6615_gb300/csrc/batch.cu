@@ -106,6 +106,11 @@ struct arp_batch {
   std::vector<unsigned char> host; // staging copy of the same layout
   std::vector<double> out;
   std::string err;
+  // one stream per group of the iteration (forked from the caller's stream after
+  // the job upload, joined back before the norms) and their events
+  std::vector<cudaStream_t> gs;
+  std::vector<cudaEvent_t> ge;
+  cudaEvent_t ready = nullptr;
 };
 
 namespace {
@@ -184,6 +189,12 @@ arp_status arp_batch_reset(arp_batch* b, arp_ctx* const* ctxs, int count) {
 
 arp_status arp_batch_destroy(arp_batch* b) {
   if (!b) return ARP_OK;
+  for (cudaStream_t g : b->gs) {
+    cudaStreamSynchronize(g);
+    cudaStreamDestroy(g);
+  }
+  for (cudaEvent_t e : b->ge) cudaEventDestroy(e);
+  if (b->ready) cudaEventDestroy(b->ready);
   if (b->dmem) cudaFree(b->dmem);
   delete b;
   return ARP_OK;
@@ -220,6 +231,11 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   // fused launches, so each gets the block size it would get on its own
   std::map<std::tuple<int, int, int>, std::vector<int>> groups;
   for (int i : act) groups[{b->ctx[i]->logN, b->ctx[i]->precision, b->ctx[i]->fine_block}].push_back(i);
+  // within a group the problems with the most fine steps per slice come first, so
+  // their (longest) blocks are dispatched first and do not form the launch's tail
+  for (auto& g : groups)
+    std::stable_sort(g.second.begin(), g.second.end(),
+                     [&](int x, int y) { return b->ctx[x]->steps > b->ctx[y]->steps; });
 
   int* first = reinterpret_cast<int*>(H + L.first);
   int nfirst = 0;  // ints used in the prefix region
@@ -337,8 +353,44 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   }
   int* dfirst = reinterpret_cast<int*>(b->dmem + L.first);
   arp_ctx* ec = b->ctx[0];  // carries launch error messages
-  for (auto& l : launches) {
+  // each group on a stream of its own after the upload (groups are independent
+  // problems), the one with the most fine work first
+  std::vector<size_t> order(launches.size());
+  std::vector<double> work(launches.size(), 0.0);
+  for (size_t li = 0; li < launches.size(); ++li) {
+    order[li] = li;
+    work[li] = (double)launches[li].fine_blocks * (1 << launches[li].logN) * launches[li].logN;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work[x] > work[y]; });
+  while (b->gs.size() < launches.size()) {
+    cudaStream_t g = nullptr;
+    cudaEvent_t e = nullptr;
+    if ((r = check_cuda(ec, cudaStreamCreateWithFlags(&g, cudaStreamNonBlocking), "batch: stream")) != ARP_OK ||
+        (r = check_cuda(ec, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "batch: event")) != ARP_OK) {
+      if (g) cudaStreamDestroy(g);
+      unswap();
+      return bfail(b, r, ec->err);
+    }
+    b->gs.push_back(g);
+    b->ge.push_back(e);
+  }
+  if (!b->ready && (r = check_cuda(ec, cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming), "batch: event")) !=
+                       ARP_OK) {
+    unswap();
+    return bfail(b, r, ec->err);
+  }
+  if ((r = check_cuda(ec, cudaEventRecord(b->ready, s), "batch: fork")) != ARP_OK) {
+    unswap();
+    return bfail(b, r, ec->err);
+  }
+  size_t forked = 0;
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    auto& l = launches[order[oi]];
     const bool f32 = (l.prec == ARP_FP32);
+    const cudaStream_t gstream = b->gs[oi];
+    if ((r = check_cuda(ec, cudaStreamWaitEvent(gstream, b->ready, 0), "batch: fork")) != ARP_OK) break;
+    forked = oi + 1;
+    cudaStream_t s = gstream;  // this group's work goes on its own stream
     if (l.nfine > 0) {
       r = f32 ? launch_fine_batch_f32(ec, l.tune, l.logN, b->dmem + l.fine_off, dfirst + l.first_fine, l.nfine, l.fine_blocks, s)
               : launch_fine_batch_f64(ec, l.tune, l.logN, b->dmem + l.fine_off, dfirst + l.first_fine, l.nfine, l.fine_blocks, s);
@@ -360,6 +412,12 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
       if ((r = run_chain(c, c->level >= 0 ? c->V : nullptr, s)) != ARP_OK) break;
     }
     if (r != ARP_OK) break;
+  }
+  // join: the caller's stream waits for every group that was forked
+  for (size_t oi = 0; oi < forked; ++oi) {
+    const arp_status q = check_cuda(ec, cudaEventRecord(b->ge[oi], b->gs[oi]), "batch: join");
+    const arp_status q2 = q == ARP_OK ? check_cuda(ec, cudaStreamWaitEvent(s, b->ge[oi], 0), "batch: join") : q;
+    if (r == ARP_OK) r = q2;
   }
   if (r == ARP_OK && !iter.empty()) {
     norm_batch_kernel<<<norm_blocks, 256, 0, s>>>(reinterpret_cast<const NormJob*>(b->dmem + L.norm),
