@@ -219,8 +219,16 @@ arp_status make_chunks(arp_ctx* c, Pipe& p, int chunk) {
   p.sf.clear();
   p.chunk = chunk;
   p.nchunks = (c->slices + chunk - 1) / chunk;
+  // the chain takes the fine results chunk by chunk, so earlier chunks' sweeps
+  // get the higher stream priority (block dispatch prefers them)
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaGetLastError();
+    least = greatest = 0;
+  }
   arp_status r;
   for (int j = 0; j < p.nchunks; ++j) {
+    const int prio = p.nchunks > 1 ? greatest + (least - greatest) * j / (p.nchunks - 1) : greatest;
     CUevent e0 = nullptr, e1 = nullptr;
     CUstream s1 = nullptr;
     {
@@ -229,7 +237,7 @@ arp_status make_chunks(arp_ctx* c, Pipe& p, int chunk) {
     }
     p.ec.push_back(e0);
     Current cur(d, p.part, p.x[1]);
-    if ((r = drv_check(c, d.greenStream(&s1, p.g[1], CU_STREAM_NON_BLOCKING, 0), "fine stream")) != ARP_OK)
+    if ((r = drv_check(c, d.greenStream(&s1, p.g[1], CU_STREAM_NON_BLOCKING, prio), "fine stream")) != ARP_OK)
       return r;
     p.sf.push_back(s1);
     if ((r = drv_check(c, d.eventCreate(&e1, CU_EVENT_DISABLE_TIMING), "event")) != ARP_OK) return r;
