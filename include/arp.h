@@ -117,11 +117,16 @@ typedef enum {
                              grid and the FFT precisions; elsewhere, or where the partition
                              cannot be made, the solve runs level by level.  Allocates one
                              more [slices][3][H] FP64 buffer on first use */
-  ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook: a non-zero value makes
-                                      block 0 of the next coarse-chain launch skip its first
-                                      grid-barrier arrival, so every block's bounded wait
-                                      gives up (after about 1 s) and the call returns
-                                      ARP_ETIMEOUT; cleared after that launch */
+  ARP_OPT_TEST_SKIP_ARRIVAL = 100  /* failure-detection test hook, cleared after one chain
+                                      launch.  1 (or any non-zero value but 2): the chain runs
+                                      as the cooperative grid and block 0 skips its first
+                                      grid-barrier arrival.  2: the chain runs in the
+                                      thread-block cluster (where one fits; ARP_OPT_CHAIN 0 or
+                                      3) and CTA 0 does not send its first partial sums.
+                                      Either way every bounded wait on them gives up (after
+                                      about 1 s) and the call returns ARP_ETIMEOUT.  Level by
+                                      level only: the pipelined solve is not taken while the
+                                      hook is set */
 } arp_option;
 
 /*

@@ -305,7 +305,7 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       c->fine_block = (int)v;
       return ARP_OK;
     case ARP_OPT_TEST_SKIP_ARRIVAL:
-      c->skip_arrival = (v != 0.0);
+      c->skip_arrival = v == 2.0 ? 2 : (v != 0.0);
       return ARP_OK;
     default:
       return fail(c, ARP_EINVAL, "unknown option key");

@@ -116,7 +116,7 @@ struct arp_batch {
 namespace {
 
 struct Layout {
-  size_t fine, chain, corr, fin, norm, first, out, total;
+  size_t fine, chain, corr, fin, norm, first, out, status, total;
 };
 
 Layout layout_for(int n) {
@@ -136,6 +136,8 @@ Layout layout_for(int n) {
   off += align256((size_t)4 * (n + 1) * sizeof(int) * 2);
   L.out = off;
   off += align256((size_t)n * sizeof(double));
+  L.status = off;  // per problem: the batched chain's status word, zero in the uploaded block
+  off += align256((size_t)n * sizeof(unsigned));
   L.total = off;
   return L;
 }
@@ -311,6 +313,7 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
         const ClusterPlan& p = plans[t];
         ClusterChainArgs a{c->level >= 0 ? c->VT : nullptr, c->U, c->Ge, c->slices, c->M, p.q, p.own, p.ph_smem,
                            p.tmp_smem, c->dT, c->inv_sig64, c->sk_sig64, c->dhalf, c->gphase};
+        a.status = reinterpret_cast<unsigned*>(b->dmem + L.status) + g.second[t];
         FinishJob fj{c->Ge, c->level >= 0 ? c->V : nullptr, c->U, c->Gc, c->H, c->K1, basis_tabs(c)};
         memcpy(H + l.fin_off + t * sizeof(FinishJob), &fj, sizeof(fj));
         first[nfirst + t] = l.fin_blocks;
@@ -429,8 +432,11 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
   if (r == ARP_OK && !iter.empty())
     r = check_cuda(ec, cudaMemcpyAsync(b->out.data(), b->dmem + L.out, iter.size() * sizeof(double),
                                        cudaMemcpyDeviceToHost, s), "batch: norm read");
-  // status words of contexts whose chain ran on its own (bounded grid barriers)
+  // status words: of the batched chains (bounded waits), and of contexts whose chain ran on its own
   std::vector<unsigned> status(n, 0u);
+  if (r == ARP_OK)
+    r = check_cuda(ec, cudaMemcpyAsync(status.data(), b->dmem + L.status, n * sizeof(unsigned),
+                                       cudaMemcpyDeviceToHost, s), "batch: status read");
   if (r == ARP_OK)
     for (auto& l : launches)
       for (int i : l.fallback)
@@ -457,7 +463,7 @@ arp_status arp_batch_iterate(arp_batch* b, void* stream, int* levels, double* ch
     if (status[i] != 0u) {
       if (is_iter[i]) std::swap(c->U, c->Uold);
       if (is_iter[i]) ++t_iter;
-      c->err = "chain: a grid barrier timed out";
+      c->err = "chain: a bounded wait timed out (a block's arrival or data never came)";
       if (first_err == ARP_OK) first_err = ARP_ETIMEOUT;
     } else if (is_iter[i]) {
       ch = b->out[t_iter++];

@@ -7,17 +7,29 @@
 // cluster.  CTA j owns the quadrature nodes [j q, (j+1) q), q = ceil(M/C), and
 // evaluates all of them at once (two FFT lanes per node), then sums their
 // weighted, back-rotated terms in node order.  The sum over CTAs, and the
-// exchange of the next state, are stores into other CTAs' shared memory
-// (distributed shared memory) between hardware cluster barriers -- no
-// global-memory atomics, no spin-waits.  Per time average:
+// exchange of the next state, are asynchronous stores into other CTAs' shared
+// memory (distributed shared memory, st.async) that each count their bytes on
+// an mbarrier of the receiving CTA -- one-way signals, no cluster-wide barrier
+// and no fence on the serial path, no global-memory atomics.  Per time average:
 //   1  every CTA: its nodes' partial sum for the current state WS, stored
 //      into the reduction buffer RED[rank] of each wavenumber's owner CTA
-//   2  cluster barrier
+//   2  the owner threads wait until their CTA's RED barrier has counted the
+//      C ranks' bytes
 //   3  CTA j, for its own (branch, wavenumber) pairs, one thread each: the sum
 //      of RED over the C ranks (fixed order), the FP64 epilogue (the midpoint
 //      state, or g and the next w), and the float copy of the result stored
 //      into WS of every CTA
-//   4  cluster barrier
+//   4  every thread waits until its CTA's WS barrier has counted the whole
+//      state (3 K1 entries); nothing reads the last link's final state, so it
+//      is not sent
+// Each barrier completes once per time average.  The next phase's byte count
+// is posted right after a wait, before this CTA sends anything that could
+// start that phase, and no phase can complete before every thread that waits
+// on it has seen the previous one (a CTA's next stores depend on its waits).
+// Every wait gives up after kBarrierTimeoutNs: the thread records ARP_ETIMEOUT
+// in the status word, its CTA leaves the loop at the next block barrier, waits
+// a bounded moment for stores in flight and meets the others at the final
+// cluster barrier, whom their own bounded waits release.
 // Only what the next link needs stays on this serial path, and GB300's FP64
 // units (1/64 of the FP32 rate) make every FP64 instruction on it costly:
 //   - the chain writes g_n = G(U_n) in the eigen basis (Ge) and leaves the
@@ -36,6 +48,7 @@
 
 #include <cooperative_groups.h>
 
+#include "chain_impl.cuh"  // globaltimer_ns, kBarrierTimeoutNs
 #include "coarse_impl.cuh"
 
 namespace arp {
@@ -55,19 +68,68 @@ struct ClusterChainArgs {
   int n0;            // index of this launch's first link
   const cd* Win;     // [3][K1] carried state w entering link n0, or null: w from U0
   cd* Wout;          // [3][K1] carried state w after the last link, or null
+  unsigned* status;  // set to ARP_ETIMEOUT if a wait gives up (0 on entry), or null
+  int skip_first;    // test hook: CTA 0 does not send its first partial sums, so the owners' waits give up
 };
+
+// mbarrier and asynchronous remote-store primitives (PTX, sm_90 and later).
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cluster_addr(unsigned local, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the phase of `parity` to complete, at most kBarrierTimeoutNs; on
+// giving up records ARP_ETIMEOUT and clears `alive` (later waits return at once).
+__device__ __forceinline__ void mbar_wait(unsigned bar, unsigned parity, unsigned* status, bool& alive) {
+  if (!alive || mbar_test(bar, parity)) return;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_test(bar, parity))
+    if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+      if (status) atomicCAS(status, 0u, (unsigned)ARP_ETIMEOUT);
+      alive = false;
+      return;
+    }
+}
+// (no memory clobber: the value travels in registers, and the volatile waits,
+// which do clobber memory, keep every later read of a received buffer after them)
+__device__ __forceinline__ void st_async(unsigned addr, cpx<float> v, unsigned bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "r"(bar));
+}
+__device__ __forceinline__ void st_async(unsigned addr, cpx<double> v, unsigned bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "d"(v.x), "d"(v.y), "r"(bar));
+}
 
 template <int LOGN> struct ClusterBlock {
   static constexpr int value = (1 << LOGN) <= 256 ? 256 : 512;
 };
 
-// Shared memory: FP64 per own wavenumber (w and e^{dT/2 D} gphase for 3
+// Shared memory: the two mbarriers (RED, WS; 16 bytes), FP64 per own wavenumber (w and e^{dT/2 D} gphase for 3
 // branches, dhalf, the two eigen constants), the FFT lanes, twiddles,
 // the node phases [q][3][K1] and weights, WS/ACC/EXCH and the eigen constants.
 template <typename T>
 inline size_t cluster_chain_smem_bytes(int logn, int q, int own, int C, bool ph_smem, bool tmp_smem) {
   const int K1 = ((1 << logn) - 1) / 3 + 1;
-  return (size_t)6 * own * sizeof(cd) + (size_t)3 * own * sizeof(double) +
+  return (size_t)16 + (size_t)6 * own * sizeof(cd) + (size_t)3 * own * sizeof(double) +
          (size_t)(2 * q * padded_len<T>(1 << logn) + twiddle_count(logn) + (ph_smem ? 3 * q * K1 : 0) + 3 * K1 +
                   (tmp_smem ? 3 * q * K1 : 0) + 3 * C * own) *
              sizeof(cpx<T>) +
@@ -93,7 +155,8 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
   // Layout, each array aligned for its element: complex FP64 arrays first
   // (16-byte elements), then complex T arrays, then FP64 scalars, then T scalars.
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cd* W64 = reinterpret_cast<cd*>(smem_raw);  // [3][own] FP64 w of the own wavenumbers
+  const unsigned bar_red = smem_addr(smem_raw), bar_ws = bar_red + 8;  // mbarriers
+  cd* W64 = reinterpret_cast<cd*>(smem_raw + 16);  // [3][own] FP64 w of the own wavenumbers
   cd* GPH = W64 + 3 * own;                    // [3][own] e^{dT/2 D} e^{-i omega dT/eps}
   cpx<T>* Z = reinterpret_cast<cpx<T>*>(GPH + 3 * own);
   cpx<T>* TW = Z + 2 * q * PL;
@@ -153,18 +216,32 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
     return (a.VT && owner_t && n < a.S) ? a.VT[((size_t)(a.n0 + n) * 3 + ob) * K1 + ok] : cd{0.0, 0.0};
   };
   cd vt_cur = load_vt(0), vt_nxt = load_vt(1);
+  // bytes per time average: the C ranks' partial sums of the own pairs, and the whole state
+  const unsigned red_bytes = (unsigned)(C * 3 * no * sizeof(cpx<T>));
+  const unsigned ws_bytes = (unsigned)(3 * K1 * sizeof(cpx<T>));
+  if (threadIdx.x == 0) {
+    mbar_init(bar_red, 1);
+    mbar_init(bar_ws, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (no > 0) mbar_expect(bar_red, red_bytes);
+    mbar_expect(bar_ws, ws_bytes);
+  }
   __syncthreads();  // W64
   for (int t = threadIdx.x; t < C * 3 * no; t += BLOCK) {
     const int c = t / (3 * no), r3 = t - c * 3 * no;
     const int b = r3 / no, r = r3 - b * no;
     cl.map_shared_rank(WS, c)[b * K1 + k0 + r] = cvt<T>(W64[b * own + r]);
   }
-  cl.sync();
+  cl.sync();  // the initial state, and the initialised barriers, visible cluster-wide
+  bool alive = true;
+  bool stop = false;
+  unsigned parity = 0;
 
 #pragma unroll 1
-  for (int n = 0; n < a.S; ++n) {
+  for (int n = 0; n < a.S && !stop; ++n) {
 #pragma unroll 1
-    for (int round = 0; round < 2; ++round) {
+    for (int round = 0; round < 2; ++round, parity ^= 1u) {
+      const bool last = n == a.S - 1 && round == 1;
       // 1: this CTA's nodes, all at once
       constexpr int ZE1 = zero_end<N>() + 1;
       for (int item = threadIdx.x; item < nq * ZE1; item += BLOCK) {
@@ -179,7 +256,10 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
         for (int b = 0; b < 3; ++b) x[b] = PH[(d * 3 + b) * K1 + k] * WS[b * K1 + k];
         pack_mode<T, N>(Z0, Z0 + PL, k, x, IS[k], SS[k]);
       }
-      __syncthreads();
+      if (__syncthreads_or(!alive)) {  // a wait of this CTA gave up
+        stop = true;
+        break;
+      }
       if (nq > 0) nonlinear_transform<T, LOGN, BLOCK>(Z, nq, TW);
       if (a.tmp_smem) {
         // weighted, back-rotated term of each (node, wavenumber)
@@ -197,7 +277,9 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
           cpx<T> s = mk<T>(0, 0);
           for (int d = 0; d < nq; ++d) s = s + TMP[d * 3 * K1 + i];
           const int b = i / K1, k = i - b * K1, owner = k / own;
-          cl.map_shared_rank(RED, owner)[(j * 3 + b) * own + (k - owner * own)] = s;
+          if (!(a.skip_first && j == 0 && n == 0 && round == 0))
+            st_async(cluster_addr(smem_addr(RED + (j * 3 + b) * own + (k - owner * own)), owner), s,
+                     cluster_addr(bar_red, owner));
         }
       } else {
         // the same sum, one thread per wavenumber over the nodes in order
@@ -211,14 +293,18 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
             for (int b = 0; b < 3; ++b) s[b] = s[b] + WM[d] * (conj(PH[(d * 3 + b) * K1 + k]) * bn[b]);
           }
           const int owner = k / own;
+          const unsigned rbar = cluster_addr(bar_red, owner);
+          if (!(a.skip_first && j == 0 && n == 0 && round == 0))
 #pragma unroll
-          for (int b = 0; b < 3; ++b) cl.map_shared_rank(RED, owner)[(j * 3 + b) * own + (k - owner * own)] = s[b];
+            for (int b = 0; b < 3; ++b)
+              st_async(cluster_addr(smem_addr(RED + (j * 3 + b) * own + (k - owner * own)), owner), s[b], rbar);
         }
       }
-      cl.sync();  // 2
       // 3: own (branch, wavenumber): sum over the ranks in rank order, FP64
       // epilogue, and the float copy of the result into every CTA's WS
       if (owner_t) {
+        mbar_wait(bar_red, parity, a.status, alive);  // 2
+        if (threadIdx.x == 0 && alive && !last) mbar_expect(bar_red, red_bytes);
         cpx<T> sr = mk<T>(0, 0);
         for (int c = 0; c < C; ++c) sr = sr + RED[(c * 3 + ob) * own + orr];
         const cd sum = cvt<double>(sr);
@@ -234,10 +320,22 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
           vt_cur = vt_nxt;
           vt_nxt = load_vt(n + 2);
         }
-        const cpx<T> vt = cvt<T>(v);
-        for (int c = 0; c < C; ++c) cl.map_shared_rank(WS, c)[ob * K1 + ok] = vt;
+        if (!last) {
+          const cpx<T> vt = cvt<T>(v);
+          const unsigned ws = smem_addr(WS + ob * K1 + ok);
+          for (int c = 0; c < C; ++c) st_async(cluster_addr(ws, c), vt, cluster_addr(bar_ws, c));
+        }
       }
-      cl.sync();  // 4
+      if (!last) {
+        mbar_wait(bar_ws, parity, a.status, alive);  // 4
+        if (threadIdx.x == 0 && alive) mbar_expect(bar_ws, ws_bytes);
+      }
+    }
+  }
+  if (__syncthreads_or(!alive)) {
+    // a wait gave up: leave stores of other CTAs still in flight a bounded moment to land
+    const unsigned long long t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 100000ull) {
     }
   }
   if (a.Wout)
@@ -327,7 +425,8 @@ arp_status launch_cluster_chain_n(arp_ctx* c, const cd* U0, cd* Ge, const cd* VT
     if (rg && rg->check_only) return ARP_OK;
     ClusterChainArgs a{VT, U0, Ge, rg ? rg->nl : c->slices, c->M, p.q, p.own, p.ph_smem, p.tmp_smem, c->dT,
                        c->inv_sig64, c->sk_sig64, c->dhalf, c->gphase, rg ? rg->n0 : 0, rg ? rg->Win : nullptr,
-                       rg ? rg->Wout : nullptr};
+                       rg ? rg->Wout : nullptr, c->sync + 1, c->skip_arrival == 2};
+    if (c->skip_arrival == 2) c->skip_arrival = 0;  // one launch
     NbarTabs<T> tb = nbar_tabs<T>(c);
     void* args[] = {&a, &tb};
     return check_cuda(c, cudaLaunchKernelExC(&cfg, kern, args), "cluster chain: launch");

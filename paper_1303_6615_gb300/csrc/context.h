@@ -147,6 +147,8 @@ inline bool fp64_grid_first(const arp_ctx* c) {
 arp_status parareal_iterate(arp_ctx* c, cudaStream_t s, int* k_done, double* change);
 // The serial chain of one context (cluster, else cooperative grid, else launches).
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s);
+// ARP_OK for a zero chain status word, else ARP_ETIMEOUT with a message.
+arp_status chain_status(arp_ctx* c, unsigned status);
 // api.cu: the coarse-grid sub-context, created or refreshed to match c's options.
 arp_status ensure_coarse(arp_ctx* c, cudaStream_t s);
 // pipeline.cu: arp_parareal_solve with the levels overlapped (the same results

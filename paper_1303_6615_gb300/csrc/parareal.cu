@@ -53,20 +53,21 @@ arp_status chain_link(arp_ctx* c, const cd* u, cd* g_out, cd* u_next, const cd* 
   return launch_nbar_reduce(c, kReduceFinal, c->partial, c->W, nullptr, g_out, v, u_next, 1, s);
 }
 
-// Reads the chain's status word; ARP_ETIMEOUT if a grid barrier gave up.
+}  // namespace
+
+// Reads the chain's status word; ARP_ETIMEOUT if a bounded wait (a grid
+// barrier, or a cluster CTA's wait for data) gave up.
 arp_status chain_status(arp_ctx* c, unsigned status) {
   if (status == 0u) return ARP_OK;
-  return fail(c, ARP_ETIMEOUT, "chain: a grid barrier timed out");
+  return fail(c, ARP_ETIMEOUT, "chain: a bounded wait timed out (a block's arrival or data never came)");
 }
-
-}  // namespace
 
 // The whole serial chain n = 0..S-1: one thread-block cluster (then the
 // parallel finish: U and the G cache from the eigen-basis g_n), else the
 // persistent cooperative kernel, else one link at a time; in FP64 the
 // cooperative kernel is tried first (ARP_OPT_CHAIN restricts the choice; the
-// barrier-timeout test hook needs the cooperative kernel, whose grid barriers
-// are the bounded waits it exercises).  V, if not
+// timeout test hook takes the cooperative kernel for value 1, whose grid
+// barriers are the bounded waits it exercises, and the cluster for value 2).  V, if not
 // null, is c->V, whose eigen form c->VT the correction kernel wrote with it.
 arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   const size_t st = (size_t)3 * c->H;
@@ -82,8 +83,15 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
     if ((r = check_cuda(c, cudaMemcpy2DAsync(q->U, q->H * sizeof(cd), c->U, c->H * sizeof(cd), q->H * sizeof(cd), 3,
                                              cudaMemcpyDeviceToDevice, s), "coarse grid: restrict u0")) != ARP_OK)
       return r;
+    if ((r = check_cuda(c, cudaMemsetAsync(q->sync, 0, 4 * sizeof(unsigned), s), "coarse grid: status reset")) !=
+        ARP_OK)
+      return r;
     r = launch_cluster_chain(q, q->U, q->Ge, V ? q->VT : nullptr, s);
     if (r != ARP_OK) return r == ARP_EINVAL ? fail(c, r, "coarse grid: no cluster chain fits") : fail(c, r, q->err);
+    // the sub-context's chain status into this context's word, which the caller reads
+    if ((r = check_cuda(c, cudaMemcpyAsync(c->sync + 1, q->sync + 1, sizeof(unsigned), cudaMemcpyDeviceToDevice, s),
+                        "coarse grid: status")) != ARP_OK)
+      return r;
     finish_kernel<<<c->slices, 256, 0, s>>>(q->Ge, V, c->U, c->Gc, c->H, c->K1, q->K1, basis_tabs(c));
     return check_cuda(c, cudaGetLastError(), "chain: finish");
   }
@@ -94,7 +102,7 @@ arp_status run_chain(arp_ctx* c, const cd* V, cudaStream_t s) {
   // first; otherwise the cluster.
   if (fp64_grid_first(c) && !c->skip_arrival) r = launch_chain(c, c->U, c->Gc, V, s);
   if (r != ARP_EINVAL) return r;
-  if ((c->chain_mode == 0 || c->chain_mode == 3) && !c->skip_arrival) {
+  if ((c->chain_mode == 0 || c->chain_mode == 3) && c->skip_arrival != 1) {
     r = launch_cluster_chain(c, c->U, c->Ge, V ? c->VT : nullptr, s);
     if (r == ARP_OK) {
       finish_kernel<<<c->slices, 256, 0, s>>>(c->Ge, V, c->U, c->Gc, c->H, c->K1, c->K1, basis_tabs(c));

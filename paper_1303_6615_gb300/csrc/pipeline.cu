@@ -64,7 +64,7 @@ struct Pipe {
   CUevent done = nullptr;             // a level's chain part and change read back (chain ctx)
   cd* Fb2 = nullptr;                  // second fine-result buffer
   cd* Wc = nullptr;                   // [3][K1] chain state carried between chunks
-  double* hchg = nullptr;             // pinned: the last level's change
+  double* hchg = nullptr;             // pinned: the last level's change, then the chain's status word
   int chunk = 0, nchunks = 0;
 };
 
@@ -283,7 +283,7 @@ arp_status make_pipe(arp_ctx* c, Pipe& p) {
   if ((r = check_cuda(c, cudaMalloc(&p.Fb2, (size_t)c->slices * 3 * c->H * sizeof(cd)), "pipeline: fine buffer")) !=
           ARP_OK ||
       (r = check_cuda(c, cudaMalloc(&p.Wc, (size_t)3 * c->K1 * sizeof(cd)), "pipeline: carried state")) != ARP_OK ||
-      (r = check_cuda(c, cudaMallocHost(&p.hchg, sizeof(double)), "pipeline: change read-back")) != ARP_OK ||
+      (r = check_cuda(c, cudaMallocHost(&p.hchg, 2 * sizeof(double)), "pipeline: change read-back")) != ARP_OK ||
       (r = drv_check(c, d.eventCreate(&p.start, CU_EVENT_DISABLE_TIMING), "event")) != ARP_OK)
     return r;
   Current cur(d, p.part, p.x[0]);
@@ -403,6 +403,10 @@ arp_status level(arp_ctx* c, Pipe& p, const Level& lv, int L, bool chain, bool f
                                            (cudaStream_t)p.sc), "pipeline: change read")) != ARP_OK)
       return r;
   }
+  // the chain's status word (sticky over the solve's levels)
+  if ((r = check_cuda(c, cudaMemcpyAsync(p.hchg + 1, c->sync + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                         (cudaStream_t)p.sc), "pipeline: status read")) != ARP_OK)
+    return r;
   return drv_check(c, d.eventRecord(p.done, p.sc), "record");
 }
 
@@ -436,9 +440,13 @@ arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, in
     Current cur(d, p.part, p.x[0]);
     if ((r = drv_check(c, d.waitEvent(p.sc, p.start, 0), "wait")) != ARP_OK) return r;
     if ((r = check_cuda(c, cudaMemcpyAsync(c->Uold, c->U, st * sizeof(cd), cudaMemcpyDeviceToDevice,
-                                           (cudaStream_t)p.sc), "pipeline: copy u0")) != ARP_OK)
+                                           (cudaStream_t)p.sc), "pipeline: copy u0")) != ARP_OK ||
+        (r = check_cuda(c, cudaMemsetAsync(c->sync, 0, 4 * sizeof(unsigned), (cudaStream_t)p.sc),
+                        "pipeline: status reset")) != ARP_OK)
       return r;
   }
+  const unsigned* hstatus = reinterpret_cast<const unsigned*>(p.hchg + 1);
+  bool unchecked = false;  // a chain level whose status word has not been read yet
   {
     Current cur(d, p.part, p.x[1]);
     for (CUstream s : p.sf)
@@ -458,6 +466,10 @@ arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, in
     return q;
   };
   auto finish = [&](arp_status status) {
+    if (status == ARP_OK && unchecked) {
+      status = drv_check(c, d.eventSync(p.done), "synchronise");
+      if (status == ARP_OK && *hstatus != 0u) status = chain_status(c, *hstatus);
+    }
     const arp_status q = join();
     if (L > L0) {
       if ((L - lv.Lb) & 1) std::swap(c->U, c->Uold);
@@ -470,6 +482,7 @@ arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, in
 
   if (L < 0) {
     if ((r = level(c, p, lv, 0, true, kmax > 0)) != ARP_OK) return finish(r);
+    unchecked = true;
     L = 0;
   } else if (L < kmax) {
     if ((r = level(c, p, lv, L, false, true)) != ARP_OK) return finish(r);
@@ -477,6 +490,8 @@ arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, in
   while (L < kmax && !(L >= 1 && ch <= c->tol)) {
     if ((r = level(c, p, lv, L + 1, true, L + 1 < kmax)) != ARP_OK) return finish(r);
     if ((r = drv_check(c, d.eventSync(p.done), "synchronise")) != ARP_OK) return finish(r);
+    unchecked = false;
+    if (*hstatus != 0u) return finish(chain_status(c, *hstatus));
     ch = *p.hchg;
     L += 1;
     if (!std::isfinite(ch)) return finish(fail(c, ARP_ENONFINITE, "parareal: relative change is not finite"));

@@ -304,17 +304,20 @@ def test_parareal_small_workload_fp32(chain):
 
 # ---------------------------------------------------------------- failure detection
 
-def test_chain_barrier_timeout_is_reported_and_context_stays_usable():
-    # Test hook: block 0 of the next chain launch skips its first barrier arrival,
-    # so every block's bounded wait gives up after about a second.
+@pytest.mark.parametrize("hook,precision", [(1, 0), (2, 0), (2, 1)],
+                         ids=["cooperative-grid", "cluster-fp64", "cluster-fp32"])
+def test_chain_barrier_timeout_is_reported_and_context_stays_usable(hook, precision):
+    # Test hook, one chain launch: 1 -- block 0 of the cooperative grid skips its
+    # first barrier arrival; 2 -- CTA 0 of the cluster does not send its first
+    # partial sums.  Every wait on them gives up after about a second.
     torch = cuda_or_skip()
     from paper_1303_6615_gb300 import binding as b
     w = ri.SMALL_N64
     p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
     u0 = w.initial_state()
-    with _solver(p, w.slices) as s:
+    with _solver(p, w.slices, precision) as s:
         b.arp_set_initial(s.ctx, to_dev(u0))
-        b.arp_set_option(s.ctx, b.ARP_OPT_TEST_SKIP_ARRIVAL, 1)
+        b.arp_set_option(s.ctx, b.ARP_OPT_TEST_SKIP_ARRIVAL, hook)
         with pytest.raises(b.ArpError) as ei:
             b.arp_parareal_iterate(s.ctx)
         assert ei.value.status == b.ARP_ETIMEOUT
@@ -325,4 +328,4 @@ def test_chain_barrier_timeout_is_reported_and_context_stays_usable():
         b.arp_get_slices(s.ctx, U)
         got = to_host(U)
     ref = o.parareal(u0, p, w.slices, 0)
-    assert per_state_rel_l2(got[1:], ref.iterates[0][1:]).max() <= TOL64
+    assert per_state_rel_l2(got[1:], ref.iterates[0][1:]).max() <= (TOL64 if precision == 0 else TOL32)
