@@ -56,13 +56,13 @@ def flops_per_grid_pt_step(n_grid: int) -> float:
 
 def solve_launches(slices: int, chunk: int, kmax: int) -> int:
     """Kernels one pipelined solve launches: per chunk of links the chain and
-    the finish (predictor), plus the correction and the per-slice change
-    (iterations), one max per iteration, and one fine launch per chunk with
-    slices at levels 0 .. kmax-1."""
+    the finish (at iterations with the per-slice change fused in), plus the
+    correction at iterations, one max per iteration, and one fine launch per
+    chunk with slices at levels 0 .. kmax-1."""
     n = -(-slices // chunk)
     fine = sum(1 for j in range(n)
                if min(slices, j * chunk + chunk + 1) > (0 if j == 0 else j * chunk + 1))
-    return 2 * n + kmax * (4 * n + 1) + kmax * fine
+    return 2 * n + kmax * (3 * n + 1) + kmax * fine
 
 
 def fine_steps(dT: float, dt: float) -> int:

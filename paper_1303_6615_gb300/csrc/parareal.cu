@@ -24,6 +24,18 @@ __global__ void finish_kernel(const cd* __restrict__ Ge, const cd* __restrict__ 
   finish_body(Ge, V, U, Gc, blockIdx.x, H, K1, K1g, tb);
 }
 
+__global__ void finish_change_kernel(const cd* __restrict__ Ge, const cd* __restrict__ V, cd* __restrict__ U,
+                                     cd* __restrict__ Gc, const cd* __restrict__ Uold, double* __restrict__ rel, int H,
+                                     int K1, int K1g, BasisTabs tb) {
+  const int n = blockIdx.x;
+  finish_body(Ge, V, U, Gc, n, H, K1, K1g, tb);
+  if (!Uold) return;
+  __syncthreads();  // the block's stores of U_{n+1}, visible to its threads
+  const size_t o1 = (size_t)(n + 1) * 3 * H;
+  const double r = slice_change_body(U + o1, Uold + o1, H);
+  if (threadIdx.x == 0) rel[n + 1] = r;
+}
+
 __global__ void slice_change_kernel(const cd* __restrict__ U, const cd* __restrict__ Uold, double* __restrict__ rel,
                                     int H) {
   const int n = blockIdx.x + 1;

@@ -128,6 +128,12 @@ __device__ __forceinline__ double max_change_body(const double* __restrict__ rel
   return bad[0] ? NAN : sm[0];
 }
 
+// One 256-thread block per slice n: finish_body, then, if Uold is not null,
+// rel[n+1] = ||U_{n+1} - Uold_{n+1}|| / ||U_{n+1}|| of the state it just wrote
+// (slice_change_body, the same tree as slice_change_kernel: the same bits).
+__global__ void finish_change_kernel(const cd* __restrict__ Ge, const cd* __restrict__ V, cd* __restrict__ U,
+                                     cd* __restrict__ Gc, const cd* __restrict__ Uold, double* __restrict__ rel, int H,
+                                     int K1, int K1g, BasisTabs tb);
 // One 256-thread block per slice n = 1..S: rel[n] = ||U_n - Uold_n|| / ||U_n||.
 __global__ void slice_change_kernel(const cd* __restrict__ U, const cd* __restrict__ Uold, double* __restrict__ rel,
                                     int H);

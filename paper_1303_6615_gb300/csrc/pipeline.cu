@@ -355,9 +355,10 @@ arp_status chain_chunk(arp_ctx* c, Pipe& p, const Level& lv, int L, int j) {
   rg.Wout = j + 1 < p.nchunks ? p.Wc : nullptr;
   rg.cluster = p.cluster;
   if ((r = launch_cluster_chain(c, U, c->Ge, L >= 1 ? c->VT : nullptr, s, &rg)) != ARP_OK) return r;
-  finish_kernel<<<nl, 256, 0, s>>>(c->Ge + a * se, L >= 1 ? c->V + a * st : nullptr, U + a * st, c->Gc + a * st, H,
-                                   K1, K1, tabs_of(c));
-  if (L >= 1) slice_change_kernel<<<nl, 256, 0, s>>>(U + a * st, lv.U(L - 1) + a * st, c->rel + a, H);
+  // U and the G cache of the chunk's links, and at iterations the per-slice change, in one launch
+  finish_change_kernel<<<nl, 256, 0, s>>>(c->Ge + a * se, L >= 1 ? c->V + a * st : nullptr, U + a * st,
+                                          c->Gc + a * st, L >= 1 ? lv.U(L - 1) + a * st : nullptr, c->rel + a, H, K1,
+                                          K1, tabs_of(c));
   if ((r = check_cuda(c, cudaGetLastError(), "pipeline: chain chunk")) != ARP_OK) return r;
   return drv_check(c, d.eventRecord(p.ec[j], p.sc), "record");
 }

@@ -7,7 +7,11 @@ resident on the device and advances all of them together: each `step()` runs
 one batched parareal level (arp_batch_iterate), so the fine sweeps and coarse
 chains of all active problems share fused launches.  A request that runs alone
 with nothing queued is finished in one arp_parareal_solve instead (its levels
-overlapped where the library pipelines them), with the same result.  Requests that arrive while
+overlapped where the library pipelines them), with the same result, when requests
+arrive more slowly than that solve takes (mean inter-arrival gap, or the time since
+the last arrival, above the remaining levels times the measured time per level of
+such solves): under heavier load the one call would hold newcomers back, so the
+request keeps advancing a level per step beside them.  Requests that arrive while
 others are running are admitted at the next step, in arrival order, as slots
 and device memory (arp_query_bytes) free up; finished problems leave the batch
 and their slices are copied to the host.
@@ -50,6 +54,17 @@ class Request:
         return self.finished - self.arrival
 
 
+def lone_solve_worthwhile(mean_gap: Optional[float], since_last: float, level_seconds: Optional[float],
+                          remaining_levels: int) -> bool:
+    """Whether a request running alone should finish in one call: with no arrival
+    history or no measured level time, yes; else when the expected gap until the
+    next arrival (the mean gap, or the time already passed since the last one if
+    longer) exceeds the time the remaining levels take."""
+    if mean_gap is None or level_seconds is None:
+        return True
+    return max(mean_gap, since_last) > remaining_levels * level_seconds
+
+
 class Server:
     """Admits requests by device memory and slot count and advances all admitted
     ones by one parareal level per step."""
@@ -72,8 +87,11 @@ class Server:
         self.next_id = 0
         # a request running alone with nothing queued finishes in one arp_parareal_solve
         # (its levels pipelined where the library can), which gives the same slices,
-        # levels and change as the batched levels
+        # levels and change as the batched levels -- while arrivals are sparse enough
         self.lone_solve = lone_solve
+        self.mean_gap: Optional[float] = None       # running mean of inter-arrival gaps (s)
+        self.last_arrival: Optional[float] = None
+        self.level_seconds: Optional[float] = None  # running mean time per level of lone solves (s)
 
     def clock(self) -> float:
         return time.perf_counter() - self.t0
@@ -82,6 +100,10 @@ class Server:
         req.rid = self.next_id
         self.next_id += 1
         req.arrival = self.clock()
+        if self.last_arrival is not None:
+            gap = req.arrival - self.last_arrival
+            self.mean_gap = gap if self.mean_gap is None else 0.75 * self.mean_gap + 0.25 * gap
+        self.last_arrival = req.arrival
         self.pending.append(req)
         return req
 
@@ -116,11 +138,16 @@ class Server:
         self._admit()
         if not self.active:
             return 0
-        if self.lone_solve and len(self.active) == 1 and not self.pending:
+        if self.lone_solve and len(self.active) == 1 and not self.pending and self._lone_ok():
             r, s = self.active[0]
             b.arp_set_option(s.ctx, b.ARP_OPT_KMAX, r.k_max)
             b.arp_set_option(s.ctx, b.ARP_OPT_TOL, r.tol)
+            lv0 = b.arp_info(s.ctx)["level"]
+            t = time.perf_counter()
             lv, ch = b.arp_parareal_solve(s.ctx, self.stream)
+            if lv > lv0:  # the call returns after the last level's change is read back
+                per = (time.perf_counter() - t) / (lv - lv0)
+                self.level_seconds = per if self.level_seconds is None else 0.75 * self.level_seconds + 0.25 * per
             levels, changes = [lv], [ch]
         else:
             self._sync_members()
@@ -140,6 +167,12 @@ class Server:
                 still.append((r, s))
         self.active = still
         return len(self.active)
+
+    def _lone_ok(self) -> bool:
+        r, s = self.active[0]
+        since = self.clock() - self.last_arrival if self.last_arrival is not None else 0.0
+        remaining = r.k_max - b.arp_info(s.ctx)["level"]
+        return lone_solve_worthwhile(self.mean_gap, since, self.level_seconds, remaining)
 
     def close(self) -> None:
         for _, s in self.active:

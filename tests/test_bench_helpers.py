@@ -1,7 +1,7 @@
 """Host-side helpers of bench.py: the kernel-launch count of one pipelined
 solve, against an enumeration of what the pipeline enqueues (per chunk of
-links: chain + finish, and at iterations also the correction and the
-per-slice change; one max per iteration; one fine launch per chunk that has
+links: chain + finish, the finish carrying the per-slice change at
+iterations, and at iterations also the correction; one max per iteration; one fine launch per chunk that has
 slices, at levels 0 .. K_max-1), and the chunking's coverage: every slice is
 swept exactly once per level, by the chunk whose chain produced its start
 state."""
@@ -17,7 +17,7 @@ def _enumerate(S, chunk, kmax):
         for j in range(n):
             a = j * chunk
             b = min(S, a + chunk)
-            launches += 2 + (2 if level >= 1 else 0)
+            launches += 2 + (1 if level >= 1 else 0)
             f0, f1 = (0 if j == 0 else a + 1), min(b + 1, S)
             if level < kmax and f1 > f0:
                 launches += 1
