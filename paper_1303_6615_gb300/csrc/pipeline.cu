@@ -7,8 +7,9 @@
 // chain of iteration k is still running on later ones.  This driver splits
 // the S links into chunks; per chunk j of level L it enqueues, on one chain
 // stream, the correction V = F - G, the cluster chain over the chunk's links
-// (its eigen-basis state carried to the next chunk exactly), the finish
-// (U_{n+1}, G cache) and the per-slice change; a fine stream per chunk runs F
+// (its eigen-basis state carried to the next chunk exactly), and the finish
+// (U_{n+1}, G cache) with the per-slice change of the states it writes in the
+// same launch; a fine stream per chunk runs F
 // on the slices whose start states that chunk produced, as soon as it is done.
 // Every kernel computes per slice or per link exactly what the level-by-level
 // iteration computes, so the result is the same bit for bit; only the order in
