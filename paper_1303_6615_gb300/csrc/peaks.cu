@@ -35,21 +35,30 @@ arp_status measure(double* tflops, cudaStream_t s) {
       per_sm < 1)
     return ARP_ECUDA;
   T* out = nullptr;
-  if (cudaMalloc(&out, sizeof(T)) != cudaSuccess) return ARP_ENOMEM;
+  if (cudaMalloc(&out, sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return ARP_ENOMEM;
+  }
   const dim3 grid(sms * per_sm * 4);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
   const T b = (T)0.999, c = (T)1e-3;
-  fma_loop_kernel<T><<<grid, 256, 0, s>>>(b, c, out);  // warm-up
-  cudaEventRecord(e0, s);
-  for (int r = 0; r < 5; ++r) fma_loop_kernel<T><<<grid, 256, 0, s>>>(b, c, out);
-  cudaEventRecord(e1, s);
-  cudaError_t err = cudaEventSynchronize(e1);
   float ms = 0.f;
+  if (err == cudaSuccess) {
+    fma_loop_kernel<T><<<grid, 256, 0, s>>>(b, c, out);  // warm-up
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+  for (int r = 0; r < 5 && err == cudaSuccess; ++r) {
+    fma_loop_kernel<T><<<grid, 256, 0, s>>>(b, c, out);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
   if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   cudaFree(out);
   if (err != cudaSuccess || ms <= 0.f) return ARP_ECUDA;
   const double flops = 5.0 * grid.x * 256.0 * kChains * kIters * 2.0;
