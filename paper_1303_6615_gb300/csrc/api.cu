@@ -223,8 +223,8 @@ arp_status arp_create(arp_ctx** out, int N, double eps, double nu, int slices, d
   c->dt = dt;
   c->steps = ratio < 1.0 ? 1 : (int)ratio;
   c->h = dT / c->steps;
-  cudaGetDevice(&c->device);
-  arp_status r = allocate(c);
+  arp_status r = check_cuda(c, cudaGetDevice(&c->device), "current device");
+  if (r == ARP_OK) r = allocate(c);
   if (r == ARP_OK) {
     cudaStream_t s;
     r = check_cuda(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");

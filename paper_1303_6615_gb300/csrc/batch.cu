@@ -157,7 +157,11 @@ arp_status arp_batch_create(arp_batch** out, arp_ctx* const* ctxs, int count) {
   if (count < 1) return ARP_EINVAL;
   arp_batch* b = new (std::nothrow) arp_batch();
   if (!b) return ARP_ENOMEM;
-  cudaGetDevice(&b->device);
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return ARP_ECUDA;
+  }
   for (int i = 0; ctxs && i < count; ++i) {
     if (!ctxs[i] || ctxs[i]->device != b->device) {
       delete b;
