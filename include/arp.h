@@ -112,8 +112,9 @@ typedef enum {
                              chain's thread-block cluster, one for the fine sweeps, which start
                              on a chunk's slices as soon as the chain has produced their start
                              states.  Results, level and change equal the level-by-level solve's
-                             bit for bit.  Applies with the cluster chain (FP32 with ARP_OPT_CHAIN
-                             0, or ARP_OPT_CHAIN 3), the asymptotic coarse scheme on the fine
+                             bit for bit.  Applies with the cluster chain (ARP_OPT_CHAIN 0 where
+                             the automatic choice is the cluster: FP32, or FP64 with M <= 16;
+                             or ARP_OPT_CHAIN 3), the asymptotic coarse scheme on the fine
                              grid and the FFT precisions; elsewhere, or where the partition
                              cannot be made, the solve runs level by level.  Allocates one
                              more [slices][3][H] FP64 buffer on first use */
@@ -220,7 +221,9 @@ arp_status arp_parareal_iterate(arp_ctx* ctx, void* stream, int* k_done,
  * the tolerance stops the solve at level k, the fine sweep of level k started
  * speculatively still completes before the work that follows on `stream`.
  * Returns after the last level's change is read; the slices are ready in
- * `stream` order.  ARP_EINVAL if no initial state was set. */
+ * `stream` order.  ARP_EINVAL if no initial state was set; ARP_ETIMEOUT if a
+ * bounded wait of the chain gave up (the iterate is then undefined until the
+ * next arp_set_initial). */
 arp_status arp_parareal_solve(arp_ctx* ctx, void* stream, int* k_done, double* max_rel_change);
 
 /* arp_get_slices: copy the current iterate U_0..U_S, [(S+1)][3][H] complex
