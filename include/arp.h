@@ -256,7 +256,10 @@ const char* arp_last_error(const arp_ctx* ctx);
  * before reading it (nothing has to start at zero); calls that overlap on the
  * GPU (on different streams, or from different threads) race on it.  The
  * first call on a device looks the array's device address up (once per
- * device), so that call should come before any stream capture.
+ * device); with lazy module loading (the CUDA default) that lookup is also
+ * what places the 16 MiB array on the device.  Make that first call at
+ * start-up, before the caller's memory budget is fixed and before any stream
+ * capture; it returns ARP_ENOMEM if the device has no room for the array.
  */
 arp_status arp_coarse_avg_static(int N, double eps, double dT, int M, const double* U_in, double* Nbar_out,
                                  int batch, void* stream);
@@ -307,8 +310,24 @@ arp_status arp_alu_peak(int precision, double* tflops, void* stream);
 /* arp_pipeline_info: how the last arp_parareal_solve ran: out[0] = 1 if
  * pipelined (ARP_OPT_PIPELINE), else 0; out[1], out[2] = SMs of the chain and
  * fine partitions, out[3] = links per chunk, out[4] = CTAs of the chain's
- * cluster (0 where no partition was made).  ARP_EINVAL for NULL arguments. */
-arp_status arp_pipeline_info(const arp_ctx* ctx, int* out5);
+ * cluster (0 where no partition was made); out[5] = 1 if a launch or call on
+ * the partitions was refused once (for instance by a profiler without support
+ * for them) while the CUDA context stayed usable: that solve was redone level
+ * by level from u0, with the same result, and the context no longer pipelines.
+ * ARP_EINVAL for NULL arguments. */
+arp_status arp_pipeline_info(const arp_ctx* ctx, int* out6);
+
+/* arp_chain_exchange_bytes: a host-side check of the cluster chain's byte
+ * counts (no GPU work, no context).  For a grid of N points, a cluster of
+ * `cluster` CTAs (1..16) and CTA `rank`, the bytes that CTA's two mbarriers
+ * expect per time average, as the chain kernel arms them: *red_bytes for the
+ * partial sums of its own (branch, wavenumber) pairs from every rank,
+ * *ws_bytes for the whole state pushed by the owners, in complex values of
+ * `precision` (ARP_FP64: 16 bytes, ARP_FP32: 8).  The paper has no
+ * counterpart; it exists so the counts can be compared with the bytes the
+ * exchanges send.  ARP_EINVAL for sizes outside those ranges or NULL pointers. */
+arp_status arp_chain_exchange_bytes(int N, int cluster, int rank, int precision, unsigned* red_bytes,
+                                    unsigned* ws_bytes);
 
 #ifdef __cplusplus
 }

@@ -51,6 +51,8 @@ _SIGS = {
     "arp_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "arp_pipeline_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "arp_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
+    "arp_chain_exchange_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_uint)]),
     "arp_coarse_avg_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P,
                                              _P, ctypes.c_int, _P]),
     "arp_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
@@ -140,10 +142,19 @@ def arp_alu_peak(precision: int, stream=None) -> float:
     return t.value
 
 
+def arp_chain_exchange_bytes(N: int, cluster: int, rank: int, precision: int) -> tuple[int, int]:
+    """(red, ws): the bytes CTA `rank` of the chain's cluster expects per time average (host arithmetic)."""
+    red, ws = ctypes.c_uint(0), ctypes.c_uint(0)
+    st = load_library().arp_chain_exchange_bytes(N, cluster, rank, precision, ctypes.byref(red), ctypes.byref(ws))
+    if st != ARP_OK:
+        raise ArpError(st, "arp_chain_exchange_bytes failed")
+    return red.value, ws.value
+
+
 def arp_pipeline_info(ctx: int) -> dict:
-    out = (ctypes.c_int * 5)()
+    out = (ctypes.c_int * 6)()
     _check(ctx, load_library().arp_pipeline_info(ctx, out))
-    keys = ("pipelined", "chain_sms", "fine_sms", "chunk", "cluster")
+    keys = ("pipelined", "chain_sms", "fine_sms", "chunk", "cluster", "refused")
     return dict(zip(keys, list(out)))
 
 

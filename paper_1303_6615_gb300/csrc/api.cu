@@ -383,7 +383,22 @@ arp_status arp_parareal_solve(arp_ctx* c, void* stream, int* k_done, double* cha
   if (pipeline_eligible(c) && c->level < c->kmax) {
     bool ran = false;
     r = parareal_solve_pipelined(c, s, &ran, k_done, change);
-    if (ran || r != ARP_OK) return r;
+    if (!ran && r != ARP_OK) {
+      // the partition or its streams could not be made: nothing was enqueued,
+      // and the pipeline stays off for this context (arp_pipeline_info)
+      cudaGetLastError();
+      c->err.clear();
+      r = ARP_OK;
+    } else if (ran && r == ARP_ECUDA && pipeline_recover(c)) {
+      // a refused call on the partitions: the level being built may be partial,
+      // so solve again from u0 (slice 0 of the iterate, never overwritten) level
+      // by level; the iterates are deterministic functions of u0, so the result
+      // is the one the pipelined solve would have returned
+      c->level = -1;
+      r = ARP_OK;
+    } else if (ran || r != ARP_OK) {
+      return r;
+    }
   }
   int k = c->level;
   double ch = INFINITY;
@@ -412,9 +427,9 @@ arp_status arp_destroy(arp_ctx* c) {
   return ARP_OK;
 }
 
-arp_status arp_pipeline_info(const arp_ctx* c, int* out5) {
-  if (!c || !out5) return ARP_EINVAL;
-  return pipeline_info(c, out5);
+arp_status arp_pipeline_info(const arp_ctx* c, int* out6) {
+  if (!c || !out6) return ARP_EINVAL;
+  return pipeline_info(c, out6);
 }
 
 const char* arp_last_error(const arp_ctx* c) {

@@ -136,6 +136,23 @@ inline size_t cluster_chain_smem_bytes(int logn, int q, int own, int C, bool ph_
          (size_t)(2 * K1 + q) * sizeof(T);
 }
 
+// Bytes CTA `rank` of a C-CTA cluster expects on its two mbarriers per time
+// average: `red`, the partial sums of its own (branch, wavenumber) pairs from
+// every rank (C x 3 x own pairs, own wavenumbers [min(K1, rank own),
+// min(K1, rank own + own))); `ws`, the whole state (3 x K1 values) pushed by
+// the owners.  elem_bytes = sizeof(cpx<T>) of the chain's precision.  The
+// kernel arms its mbarriers with these counts; arp_chain_exchange_bytes
+// returns them to the host.
+struct ChainExchangeBytes {
+  unsigned red, ws;
+};
+__host__ __device__ inline ChainExchangeBytes chain_exchange_bytes(int K1, int C, int rank, int own,
+                                                                   int elem_bytes) {
+  const int k0 = rank * own < K1 ? rank * own : K1;
+  const int k1 = k0 + own < K1 ? k0 + own : K1;
+  return {(unsigned)(C * 3 * (k1 - k0) * elem_bytes), (unsigned)(3 * K1 * elem_bytes)};
+}
+
 template <typename T, int LOGN, int BLOCK>
 __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, const NbarTabs<T>& tb) {
   namespace cg = cooperative_groups;
@@ -217,8 +234,9 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
   };
   cd vt_cur = load_vt(0), vt_nxt = load_vt(1);
   // bytes per time average: the C ranks' partial sums of the own pairs, and the whole state
-  const unsigned red_bytes = (unsigned)(C * 3 * no * sizeof(cpx<T>));
-  const unsigned ws_bytes = (unsigned)(3 * K1 * sizeof(cpx<T>));
+  const ChainExchangeBytes xb = chain_exchange_bytes(K1, C, j, own, (int)sizeof(cpx<T>));
+  const unsigned red_bytes = xb.red;
+  const unsigned ws_bytes = xb.ws;
   if (threadIdx.x == 0) {
     mbar_init(bar_red, 1);
     mbar_init(bar_ws, 1);

@@ -157,6 +157,11 @@ arp_status ensure_coarse(arp_ctx* c, cudaStream_t s);
 bool pipeline_eligible(const arp_ctx* c);
 arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, int* k_done, double* change);
 arp_status pipeline_info(const arp_ctx* c, int* out);
+// After a pipelined solve that ran and failed with ARP_ECUDA: true if the CUDA
+// context is still usable (a launch or call on the SM partitions was refused,
+// e.g. by a profiler that does not support them, rather than a fault); the
+// pipeline is then disabled for c and the caller solves level by level.
+bool pipeline_recover(arp_ctx* c);
 void pipeline_release(arp_ctx* c);
 // dftgemm.cu: the DFT-as-GEMM precisions (ARP_TF32X3, ARP_BF16X2): the time
 // average's node terms as one chunk partial [batch][1][3][K1], and the ETDRK4

@@ -52,6 +52,7 @@ struct Partition {
 
 struct Pipe {
   bool built = false, ok = false;
+  bool refused = false;               // a call on the partitions failed once; the context solves level by level
   std::string why;                    // why the pipeline is unavailable
   Partition* part = nullptr;          // the shared partition (not owned)
   CUgreenCtx g[2] = {nullptr, nullptr};  // its green contexts: 0 chain, 1 fine
@@ -302,6 +303,7 @@ arp_status ensure_pipe(arp_ctx* c) {
   Pipe& p = *c->pipe;
   const int S = c->slices;
   const int chunk = c->pipeline >= 2 ? std::min(c->pipeline, S) : std::max(4, (S + 15) / 16);
+  if (p.refused) return ARP_OK;
   arp_status r = ARP_OK;
   if (!p.built) {
     p.built = true;
@@ -501,6 +503,26 @@ arp_status parareal_solve_pipelined(arp_ctx* c, cudaStream_t user, bool* ran, in
   return finish(ARP_OK);
 }
 
+bool pipeline_recover(arp_ctx* c) {
+  Pipe* p = c->pipe;
+  if (!p || !p->ok) return false;
+  const std::string cause = c->err;
+  cudaGetLastError();  // a refused launch leaves a non-sticky error behind
+  bool usable = true;
+  if (p->sc && cudaStreamSynchronize((cudaStream_t)p->sc) != cudaSuccess) usable = false;
+  for (CUstream s : p->sf)
+    if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess) usable = false;
+  if (cudaDeviceSynchronize() != cudaSuccess) usable = false;
+  cudaGetLastError();
+  if (!usable) return false;  // a fault: the context is lost, nothing to fall back to
+  p->ok = false;
+  p->refused = true;
+  p->why = "a call on the SM partitions failed (" + cause + "); this context solves level by level";
+  c->last_pipelined = 0;
+  c->err.clear();
+  return true;
+}
+
 arp_status pipeline_info(const arp_ctx* c, int* out) {
   const Pipe* p = c->pipe;
   out[0] = c->last_pipelined;
@@ -508,6 +530,7 @@ arp_status pipeline_info(const arp_ctx* c, int* out) {
   out[2] = p && p->ok ? p->sms[1] : 0;
   out[3] = p && p->ok ? p->chunk : 0;
   out[4] = p && p->ok ? p->cluster : 0;
+  out[5] = p && p->refused ? 1 : 0;
   return ARP_OK;
 }
 

@@ -10,7 +10,11 @@
 // kStaticScratchBytes, which every GPU that loads the library holds until the
 // process exits, and runs the same table, time-average and reduction kernels
 // as arp_coarse_avg on it.  It never calls cudaMalloc, cudaFree or any other
-// allocating routine.
+// allocating routine.  With lazy module loading (the CUDA default) the array
+// is placed on a device by the first call there (the symbol lookup loads this
+// module), so callers make one call per device at start-up, before their
+// memory budget is fixed and before any stream capture; if the device has no
+// room left at that point the call returns ARP_ENOMEM.
 #include <cmath>
 #include <mutex>
 
@@ -82,7 +86,13 @@ extern "C" arp_status arp_coarse_avg_static(int N, double eps, double dT, int M,
   const int chunk = (int)((kStaticScratchBytes - tables - 512) / per_state);
 
   unsigned char* base = nullptr;
-  if (scratch_address(c.device, &base) != cudaSuccess) return ARP_ECUDA;
+  const cudaError_t se = scratch_address(c.device, &base);
+  if (se != cudaSuccess) {
+    cudaGetLastError();
+    // the array is placed on the device when this module loads, which under
+    // lazy module loading is this first lookup: no room left means ARP_ENOMEM
+    return se == cudaErrorMemoryAllocation ? ARP_ENOMEM : ARP_ECUDA;
+  }
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     unsigned char* p = base + off;

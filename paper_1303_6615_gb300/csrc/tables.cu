@@ -165,19 +165,21 @@ __global__ void weights_kernel(int M, double* w64, float* w32) {
 // phase[m][b][k] = e^{-i omega s_m}, s_m = T0 m / M.
 __global__ void phase_kernel(int M, int K1, double s, double T0, cd* ph64, cf* ph32) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = blockIdx.y;
   if (k >= K1) return;
-  const double sm = T0 * (double)m / (double)M;
-  const double arg = omega_of(2, k, s) * sm;
-  double sn, cs;
-  sincos(arg, &sn, &cs);
-  const size_t base = (size_t)m * 3 * K1;
-  ph64[base + 2 * K1 + k] = {cs, -sn};
-  ph64[base + 0 * K1 + k] = {cs, sn};
-  ph64[base + 1 * K1 + k] = {1.0, 0.0};
-  ph32[base + 2 * K1 + k] = {(float)cs, -(float)sn};
-  ph32[base + 0 * K1 + k] = {(float)cs, (float)sn};
-  ph32[base + 1 * K1 + k] = {1.0f, 0.0f};
+  // nodes strided over gridDim.y (at most 65535 rows of blocks), so any M works
+  for (int m = blockIdx.y; m < M; m += gridDim.y) {
+    const double sm = T0 * (double)m / (double)M;
+    const double arg = omega_of(2, k, s) * sm;
+    double sn, cs;
+    sincos(arg, &sn, &cs);
+    const size_t base = (size_t)m * 3 * K1;
+    ph64[base + 2 * K1 + k] = {cs, -sn};
+    ph64[base + 0 * K1 + k] = {cs, sn};
+    ph64[base + 1 * K1 + k] = {1.0, 0.0};
+    ph32[base + 2 * K1 + k] = {(float)cs, -(float)sn};
+    ph32[base + 0 * K1 + k] = {(float)cs, (float)sn};
+    ph32[base + 1 * K1 + k] = {1.0f, 0.0f};
+  }
 }
 
 // dhalf[k] = e^{-nu k^4 dT/2}; gphase[b][k] = e^{-i omega dT/eps};
@@ -214,7 +216,7 @@ arp_status build_tables(arp_ctx* c, cudaStream_t st) {
   twiddle_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw64, c->tw32);
   etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32);
   weights_kernel<<<1, 256, 0, st>>>(c->M, c->weight64, c->weight32);
-  phase_kernel<<<dim3((c->K1 + tb - 1) / tb, c->M), tb, 0, st>>>(c->M, c->K1, s, T0, c->phase64, c->phase32);
+  phase_kernel<<<dim3((c->K1 + tb - 1) / tb, c->M < 65535 ? c->M : 65535), tb, 0, st>>>(c->M, c->K1, s, T0, c->phase64, c->phase32);
   coarse_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->nu, c->dT, inv_eps, c->dhalf, c->gphase,
                                                                c->strang_h64);
   arp_status r = check_cuda(c, cudaGetLastError(), "table kernels");

@@ -112,3 +112,42 @@ def test_projection_and_parseval():
     # Parseval: mean over the grid of sum_f u_f(x)^2 equals the squared norm.
     x = o.synthesize(pu, n)
     np.testing.assert_allclose(np.mean(np.sum(x ** 2, axis=0)), o.parseval_norm(pu) ** 2, rtol=1e-13)
+
+
+def test_physical_linf_closed_form_and_axes():
+    # The error metric of Sec. 6.2's experiments: the largest |u_f(x_j)| over the
+    # grid points and the three fields, per state.  A two-mode state has it in
+    # closed form: v1 = a cos x (u_1 = a/2) peaks at x = 0, h = b sin 2x
+    # (u_2 = -i b/2) peaks at x = pi/4, both grid points for N = 8; v2 = 0.
+    n = 8
+    H = n // 2 + 1
+    states = []
+    for a, b in ((0.3, -1.7), (-2.5, 0.4), (0.0, 0.0)):
+        u = np.zeros((3, H), dtype=np.complex128)
+        u[0, 1] = a / 2.0
+        u[2, 2] = -0.5j * b
+        states.append(u)
+    batch = np.stack(states)                       # (3 states, 3 fields, H)
+    got = o.physical_linf(batch, n)
+    assert got.shape == (3,)
+    np.testing.assert_allclose(got, [1.7, 2.5, 0.0], rtol=1e-14, atol=1e-15)
+    # a hand-written synthesis, term by term over -N/2 < k <= N/2, on a random
+    # band-limited batch with two leading axes
+    rng = np.random.default_rng(9)
+    n = 16
+    H = n // 2 + 1
+    uh = rng.standard_normal((2, 2, 3, H)) + 1j * rng.standard_normal((2, 2, 3, H))
+    uh[..., 0] = uh[..., 0].real
+    uh[..., H - 1] = 0.0
+    want = np.zeros((2, 2))
+    for idx in np.ndindex(2, 2):
+        best = 0.0
+        for f in range(3):
+            for j in range(n):
+                x = 2.0 * math.pi * j / n
+                s = uh[idx][f, 0].real
+                for k in range(1, H - 1):
+                    s += 2.0 * (uh[idx][f, k] * complex(math.cos(k * x), math.sin(k * x))).real
+                best = max(best, abs(s))
+        want[idx] = best
+    np.testing.assert_allclose(o.physical_linf(uh, n), want, rtol=1e-13)

@@ -44,6 +44,14 @@ def _bad_apply(m, u):
     return np.einsum("kji,...jk->...ik", m, u)   # transposed operand
 
 
+def _bad_linf_grid_axis_only(u, n):
+    return np.max(np.abs(rsw.synthesize(u, n)), axis=-1)       # reduces the grid axis only
+
+
+def _bad_linf_unscaled(u, n):
+    return np.max(np.abs(np.fft.irfft(u, n=n, axis=-1)), axis=(-2, -1))   # drops the factor N
+
+
 def _bad_quadrature(p):
     s, w = _orig["quadrature"](p)
     return s + p.window / p.m_quad / 2, w        # nodes shifted by half a spacing
@@ -77,7 +85,8 @@ def _bad_ifrk4_stage(u, p, h, nl=None):
 
 
 _orig = {name: getattr(rsw, name) for name in
-         ("nonlinear", "phi123", "etdrk4_coefficients", "expL", "_apply", "quadrature", "strang_step", "ifrk4_step")}
+         ("nonlinear", "phi123", "etdrk4_coefficients", "expL", "_apply", "quadrature", "strang_step", "ifrk4_step",
+          "physical_linf")}
 
 CASES = [
     ("nonlinear", _bad_nl_sign, tm.test_nonlinearity_analytic_case, ()),
@@ -91,6 +100,8 @@ CASES = [
     ("strang_step", _bad_strang_one_half_step, ts.test_strang_linear_part_is_exact, ()),
     ("strang_step", _bad_strang_stage_from_u, ts.test_strang_second_order_convergence, ()),
     ("ifrk4_step", _bad_ifrk4_stage, ts.test_ifrk4_fourth_order_and_invariants, ()),
+    ("physical_linf", _bad_linf_grid_axis_only, tm.test_physical_linf_closed_form_and_axes, ()),
+    ("physical_linf", _bad_linf_unscaled, tm.test_physical_linf_closed_form_and_axes, ()),
 ]
 
 

@@ -50,3 +50,23 @@ def test_static_time_average_rejects_sizes_beyond_its_array():
     with pytest.raises(b.ArpError) as ei:
         b.arp_coarse_avg_static(n, 1e-3, 0.01, 4096, x, torch.empty_like(x))
     assert ei.value.status == b.ARP_EINVAL
+
+
+def test_static_time_average_several_passes_against_oracle():
+    # 40 states at N = 512, M = 64: more than one pass through the array holds
+    # (29 states), so the batch runs in two passes.  Checked against the
+    # context path and directly against the oracle's time average (Eq. 2.1,
+    # Algorithm 1).
+    torch = cuda_or_skip()
+    from oracle import rsw as o
+    from paper_1303_6615_gb300 import binding as b
+    n, eps, dT, m = 512, 1e-3, 10 / 256, 64
+    x = ri.random_batch(n, 32, 256.0, 40, 500) * 512.0
+    xin = to_dev(x)
+    out = torch.full_like(xin, float("nan"))
+    b.arp_coarse_avg_static(n, eps, dT, m, xin, out)
+    got = to_host(out)
+    assert np.all(np.isfinite(got))
+    assert per_state_rel_l2(got, _reference(b, n, eps, dT, m, x)).max() <= TOL64
+    p = o.Params(n, eps, 1e-4, dT, dT / 8, m)
+    assert per_state_rel_l2(got, o.nbar(x, p)).max() <= TOL64
