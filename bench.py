@@ -1,20 +1,25 @@
 #!/usr/bin/env python
 """Throughput of the asymptotic parareal hot path on one GB300.
 
-Workload (the single large instance): 1D rotating shallow water, N = 512
-grid points, eps = 1e-3, nu = 1e-4, T = 10 over 256 slices, fine ETDRK4 step
-dt = 1e-4 (391 steps of 9.99e-5 per slice), M = 64 quadrature points, seeded
-synthetic initial spectrum (|k| <= 32, scale e^{-k^2/256}).
+Headline workload (the largest single-GPU configuration, the precision-sweep
+instance): 1D rotating shallow water, N = 1024 grid points, eps = 1e-4,
+nu = 1e-4, T = 10 over 512 slices, fine ETDRK4 step dt = 1e-5 (1954 steps of
+9.995e-6 per slice), M = 128 quadrature points, seeded synthetic initial
+spectrum (|k| <= 32, scale e^{-k^2/256}).
 
 One timed step = one complete parareal solve through the C ABI
 (arp_set_initial + arp_parareal_solve with K_max = 5): the coarse predictor
-and five iterations, each a fine sweep of all 256 slices, V = F - G, the
-serial chain of 256 coarse steps and the convergence norm, pipelined across
-iterations (ARP_OPT_PIPELINE).  Metric: fine grid-point-steps per second =
-5 sweeps * slices * N * fine steps / step time.
+and five iterations, each a fine sweep of all slices, V = F - G, the serial
+chain of coarse steps and the convergence norm, pipelined across iterations
+(ARP_OPT_PIPELINE).  Metric: fine grid-point-steps per second = 5 sweeps *
+slices * N * fine steps / step time.  Beside it the line carries the same
+solve on the single large instance (N = 512, 256 slices, M = 64), the time to
+1e-5 relative error of the FP32-bulk solve against the plain FP64 GPU path,
+serving latency (p50/p99) at one seeded Poisson rate, and the FP64 oracle on
+the host cores, single-threaded and in parallel over slices.
 
 --impl reference times the FP64 CPU oracle instead (one iteration restricted
-to 8 slices per step, on the host cores).
+to 2 slices per step, on the host cores).
 """
 from __future__ import annotations
 
@@ -34,17 +39,19 @@ if ROOT not in sys.path:
 
 import rsw_inputs as ri  # noqa: E402
 
-WORKLOAD = ri.LARGE_N512
+WORKLOAD = ri.SWEEP_N1024       # headline: the largest single-GPU configuration
+LARGE = ri.LARGE_N512            # the single large instance, reported beside it
 METRIC = "fine grid-pt-steps/s"
 # FP32 peak of the plain ALUs: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # FP64 peak: the part's nominal 1.25 TFLOP/s (FP64 units are a small fraction of FP32 ones).
 FP64_ALU_PEAK_TFLOPS = 1.25
-CPU_SAMPLE_SLICES = 64          # cpu_baseline sample (about 10 s of oracle work)
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fine-sweep kernel on this workload
+CPU_SAMPLE_SLICES = 8           # cpu_baseline sample, one core (about 10-20 s of oracle work at N = 1024)
+CPU_PARALLEL_SLICES_PER_CORE = 2  # cpu_baseline sample in parallel over slices: slices per host core
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fine-sweep kernel on a workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
-FINE_TRAFFIC_BYTES = {"fp32": 2256896, "fp64": None}
-REFERENCE_SAMPLE_SLICES = 8     # per-step sample of the reference arm
+FINE_TRAFFIC_BYTES = {}
+REFERENCE_SAMPLE_SLICES = 2     # per-step sample of the reference arm
 
 
 def flops_per_grid_pt_step(n_grid: int) -> float:
@@ -77,6 +84,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the headline solve (no N=512 solve, time to 1e-5 or serving keys)")
     ap.add_argument("--mode", choices=["headline", "tts", "precision", "batched", "serve", "paper", "schemes",
                                        "coarsegrid", "dftgemm", "kernels"],
                     default="headline",
@@ -175,7 +184,10 @@ def job_throughput(units_per_step: float, steps: int, world: int, max_ms: float)
     return units_per_step * steps * world / (max_ms / 1e3)
 
 
-def run_ours(args, rank: int, world: int) -> dict | None:
+def run_ours(args, rank: int, world: int, w=None, timed_steps: int | None = None) -> dict | None:
+    """The contract line for workload w (default: the headline workload): complete
+    solves timed on the device, the level-by-level solve beside them, the dominant
+    kernel's own launch for the roofline, and the end-to-end solve with host buffers."""
     import torch
     import torch.distributed as dist
 
@@ -189,7 +201,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     if world > 1:
         dist.barrier()
     b.load_library()
-    w = WORKLOAD
+    w = w or WORKLOAD
+    nsteps = timed_steps or args.steps
     steps = fine_steps(w.dT, w.dt)
     units = w.slices * w.n_grid * steps  # fine grid-point-steps per iteration
     prec = b.ARP_FP32 if args.precision == "fp32" else b.ARP_FP64
@@ -210,7 +223,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         solve()
     # inputs are far smaller than L2 (129 MB): flush L2 between timed steps
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
@@ -218,7 +231,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         dist.barrier()
     torch.cuda.synchronize()
     changes = []
-    for i in range(args.steps):
+    for i in range(nsteps):
         flush.zero_()
         ev[i][0].record(stream)
         k_done, ch = solve()
@@ -231,14 +244,14 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     pinfo = b.arp_pipeline_info(ctx)
     step_ms = [a.elapsed_time(z) for a, z in ev]
     total_ms = max_over_ranks(sum(step_ms), world, "cuda")
-    value = job_throughput(sweeps * units, args.steps, world, total_ms)
+    value = job_throughput(sweeps * units, nsteps, world, total_ms)
     launches = solve_launches(w.slices, pinfo["chunk"], kmax) if pinfo["pipelined"] else 5 * kmax + 2
 
     # the same solves level by level (no overlap of iterations), for comparison
     b.arp_set_option(ctx, b.ARP_OPT_PIPELINE, 0)
     solve()
     lbl = []
-    for _ in range(min(args.steps, 5)):
+    for _ in range(min(nsteps, 5)):
         flush.zero_()
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -292,9 +305,9 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "value": value,
         "unit": "grid-pt-steps/s",
         "n_gpus": world,
-        "steps": args.steps,
+        "steps": nsteps,
         "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps,
+        "ms_per_step": total_ms / nsteps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -309,7 +322,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": FINE_TRAFFIC_BYTES[args.precision],
+                     "frac": achieved / peak, "traffic": FINE_TRAFFIC_BYTES.get((w.name, args.precision)),
                      "kernel": "fine_sweep_kernel_f32" if prec == b.ARP_FP32 else "fine_sweep_kernel",
                      "launch_ms": fine_ms, "flop_per_launch": flops,
                      "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec == b.ARP_FP32
@@ -322,7 +335,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                 "step": f"complete solve: predictor + {kmax} iterations, host buffers", "seconds": e2e_s},
         "level_by_level": {"value": sweeps * units / (lbl_ms / 1e3), "unit": "grid-pt-steps/s",
                            "ms_per_step": lbl_ms, "note": "the same solves with ARP_OPT_PIPELINE 0"},
-        "gpu_launches": args.steps * launches,
+        "gpu_launches": nsteps * launches,
         "clocks": clk,
         "last_rel_change": changes[-1] if changes else None,
         "k_done": k_done,
@@ -331,28 +344,114 @@ def run_ours(args, rank: int, world: int) -> dict | None:
 
 # ----------------------------------------------------------------------------- oracle on the host
 
-def oracle_iteration_sample(slices: int):
-    """One parareal iteration of the FP64 oracle on the first `slices` slices of
-    the workload, starting from the predictor; returns (seconds, units)."""
-    import numpy as np  # noqa: F401
+def _oracle_params(w):
+    from oracle import rsw as o
+    return o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+
+
+def oracle_predictor(slices: int, w=None):
+    """The oracle's coarse predictor U^0 on the first `slices` slices of workload w."""
+    import numpy as np
 
     from oracle import rsw as o
-    w = WORKLOAD
-    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
-    u0 = o.project(w.initial_state(), w.n_grid)
-    U = [u0]
+    w = w or WORKLOAD
+    p = _oracle_params(w)
+    U = [o.project(w.initial_state(), w.n_grid)]
     for _ in range(slices):
         U.append(o.coarse_step(U[-1], p))
-    import numpy as np
-    U = np.stack(U)
+    return np.stack(U)
+
+
+def oracle_iteration_sample(slices: int, w=None, U=None):
+    """One parareal iteration of the FP64 oracle on the first `slices` slices of
+    workload w, starting from the predictor (computed untimed unless given);
+    one host core.  Returns (seconds, fine grid-point-steps of the sample)."""
+    from oracle import rsw as o
+    w = w or WORKLOAD
+    p = _oracle_params(w)
+    U = oracle_predictor(slices, w) if U is None else U
     t0 = time.perf_counter()
     f_old = o.fine_propagate(U[:-1], p)
     g_old = o.coarse_step(U[:-1], p)
-    new = [u0]
+    new = [U[0]]
     for n in range(1, slices + 1):
         new.append(o.coarse_step(new[n - 1], p) + f_old[n - 1] - g_old[n - 1])
     dt = time.perf_counter() - t0
     return dt, slices * w.n_grid * fine_steps(w.dT, w.dt)
+
+
+def _oracle_parallel_part(task):
+    """Worker of the parallel oracle: F and G of one block of slices (the part
+    of an iteration that is independent per slice)."""
+    params, states = task
+    from oracle import rsw as o
+    p = o.Params(*params)
+    return o.fine_propagate(states, p), o.coarse_step(states, p)
+
+
+def _oracle_worker_ready(_):
+    from oracle import rsw  # noqa: F401  (import cost paid before the timed region)
+    return os.getpid()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_iteration_parallel(cores: int, per_core: int, w=None):
+    """One parareal iteration of the FP64 oracle on cores x per_core slices of
+    workload w, with F and G of the slices spread over `cores` worker processes
+    (started with spawn, warmed up before the timed region) and the serial chain
+    in this process.  Returns (seconds, units, slices)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import numpy as np
+
+    from oracle import rsw as o
+    w = w or WORKLOAD
+    slices = cores * per_core
+    p = _oracle_params(w)
+    U = oracle_predictor(slices, w)
+    params = (w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+    # one numerical thread per worker: the cores are the workers
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_oracle_worker_ready, range(cores)))
+            t0 = time.perf_counter()
+            blocks = [U[i * per_core:(i + 1) * per_core] for i in range(cores)]
+            parts = list(ex.map(_oracle_parallel_part, [(params, blk) for blk in blocks]))
+            f_old = np.concatenate([f for f, _ in parts])
+            g_old = np.concatenate([g for _, g in parts])
+            new = [U[0]]
+            for n in range(1, slices + 1):
+                new.append(o.coarse_step(new[n - 1], p) + f_old[n - 1] - g_old[n - 1])
+            dt = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return dt, slices * w.n_grid * fine_steps(w.dT, w.dt), slices
 
 
 def cpu_cores_used() -> int:
@@ -365,8 +464,9 @@ def run_reference(args, rank: int) -> dict | None:
         return None
     w = WORKLOAD
     times, units = [], 0
+    U = oracle_predictor(REFERENCE_SAMPLE_SLICES, w)
     for i in range(args.warmup + args.steps):
-        dt, units = oracle_iteration_sample(REFERENCE_SAMPLE_SLICES)
+        dt, units = oracle_iteration_sample(REFERENCE_SAMPLE_SLICES, w, U)
         if i >= args.warmup:
             times.append(dt)
     total = sum(times)
@@ -405,7 +505,7 @@ def _parseval(a):
     return np.sqrt(np.sum(wgt * np.abs(a) ** 2, axis=(-2, -1)))
 
 
-def run_tts(args) -> dict:
+def run_tts(args, w=None) -> dict:
     """Time to the first parareal iterate within 1e-5 (max over slices of the relative
     L2 error) of the serial fine solution, for the FP32-bulk and the plain FP64 path,
     one instance each, end to end through the C ABI with host buffers (u0 in;
@@ -418,7 +518,7 @@ def run_tts(args) -> dict:
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
-    w = WORKLOAD
+    w = w or LARGE
     H = w.n_grid // 2 + 1
     t0 = time.perf_counter()
     ser = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
@@ -613,7 +713,7 @@ def run_schemes(args) -> dict:
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
-    w = WORKLOAD
+    w = LARGE
     names = {0: "etdrk4", 1: "strang", 2: "ifrk4"}
     out = {"mode": "schemes", "workload": w.name, "sweep": {}, "accuracy": {}}
     x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, w.slices, 9)).cuda()
@@ -670,7 +770,7 @@ def run_coarsegrid(args) -> dict:
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
-    w = WORKLOAD
+    w = LARGE
     H = w.n_grid // 2 + 1
     u0 = torch.from_numpy(w.initial_state()).cuda()
     ser = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")
@@ -715,16 +815,17 @@ def run_dftgemm(args) -> dict:
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
-    w = WORKLOAD
+    w = LARGE
     if args.probe:
-        # one time average in ARP_TF32X3 on 16 states, twice: a small case for a profiler
-        x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, 16, 9)).cuda()
+        # one time average per split precision on 64 states (4096 column groups), twice: a small case for a profiler
+        x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, 64, 9)).cuda()
         y = torch.empty_like(x)
-        with b.Solver(w.n_grid, w.eps, w.nu, 16, w.dT, w.dt, w.m_quad, precision=b.ARP_TF32X3) as s:
-            for _ in range(2):
-                b.arp_coarse_avg(s.ctx, x, y)
+        for prec in (b.ARP_TF32X3, b.ARP_BF16X3):
+            with b.Solver(w.n_grid, w.eps, w.nu, 64, w.dT, w.dt, w.m_quad, precision=prec) as s:
+                for _ in range(2):
+                    b.arp_coarse_avg(s.ctx, x, y)
         torch.cuda.synchronize()
-        return {"mode": "dftgemm", "probe": "one ARP_TF32X3 time average of 16 states, twice"}
+        return {"mode": "dftgemm", "probe": "one ARP_TF32X3 and one ARP_BF16X3 time average of 64 states, twice each"}
     x = torch.from_numpy(ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, w.slices, 9)).cuda()
     y = torch.empty_like(x)
     steps = fine_steps(w.dT, w.dt)
@@ -745,18 +846,20 @@ def run_dftgemm(args) -> dict:
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    for name, prec in (("fp32_fft", b.ARP_FP32), ("tf32x3_gemm", b.ARP_TF32X3), ("bf16x2_gemm", b.ARP_BF16X2)):
+    products = {b.ARP_TF32X3: 3, b.ARP_BF16X2: 4, b.ARP_BF16X3: 6}
+    for name, prec in (("fp32_fft", b.ARP_FP32), ("tf32x3_gemm", b.ARP_TF32X3), ("bf16x2_gemm", b.ARP_BF16X2),
+                       ("bf16x3_gemm", b.ARP_BF16X3)):
         with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
             ms = timed(lambda: b.arp_fine_batch(s.ctx, x, y), 3)
             units = w.slices * N * steps
-            # dense work per step: 4 evaluations x (4 inverse + 3 forward columns) x 2 N R flops x 3 split products
-            dense = w.slices * steps * 4 * 7 * 2 * N * R * 3
+            # dense work per step: 4 evaluations x (4 inverse + 3 forward columns) x 2 N R flops x split products
+            dense = w.slices * steps * 4 * 7 * 2 * N * R * products.get(prec, 0)
             out["fine_sweep"][name] = {"ms": ms, "algorithmic_tflops": units * flops_per_grid_pt_step(N) / ms / 1e9,
                                        "dense_gemm_tflops": dense / ms / 1e9 if prec != b.ARP_FP32 else None}
             ms = timed(lambda: b.arp_coarse_avg(s.ctx, x, y), 5)
             nodes = w.slices * w.m_quad
             fft_flops = nodes * N * (35.0 * math.log2(N) + 64.0)  # one N-evaluation per node
-            dense = nodes * 7 * 2 * N * R * 3
+            dense = nodes * 7 * 2 * N * R * products.get(prec, 0)
             out["time_average"][name] = {"ms": ms, "algorithmic_tflops": fft_flops / ms / 1e9,
                                          "dense_gemm_tflops": dense / ms / 1e9 if prec != b.ARP_FP32 else None}
     return out
@@ -981,6 +1084,48 @@ def run_serve(args) -> dict:
     return out
 
 
+def serve_one_rate(rate: float = 100.0, count: int = 64, seed: int = 3000) -> dict:
+    """Serving latency at one seeded Poisson rate: `count` requests (serve_requests)
+    through the continuous-batching FP32 server, and the plain FP64 path serving
+    the same requests one at a time in arrival order (each request's FP64 service
+    time measured alone on the GPU)."""
+    import numpy as np
+    import torch
+
+    from paper_1303_6615_gb300 import binding as b
+    from paper_1303_6615_gb300 import serve
+    rng = np.random.default_rng(int(rate))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    reqs = serve_requests(count, seed)
+    server = serve.Server(memory_budget=24 << 30, max_active=256, precision=b.ARP_FP32, lone_solve=True)
+    try:
+        t0 = server.clock()
+        done = serve.replay(server, list(zip(arrivals.tolist(), reqs)))
+        makespan = server.clock() - t0
+    finally:
+        server.close()
+    lat = np.array([r.latency for r in done])
+    service64 = []
+    for r in serve_requests(count, seed):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        serve.solve_alone(r, b.ARP_FP64)
+        torch.cuda.synchronize()
+        service64.append(time.perf_counter() - t1)
+    finish, lat64 = 0.0, []
+    for a, sv in zip(arrivals, service64):
+        finish = max(finish, a) + sv
+        lat64.append(finish - a)
+    lat64 = np.array(lat64)
+    return {"rate_req_s": rate, "requests": count, "seed": seed,
+            "requests_mix": "N 128-2048, eps 1e-4-1e-2, 32-512 slices, T 0.1-1, M 32, K_max 5 or change <= 1e-8",
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "throughput_req_s": count / makespan,
+            "fp64_one_at_a_time": {"p50_ms": 1e3 * float(np.percentile(lat64, 50)),
+                                   "p99_ms": 1e3 * float(np.percentile(lat64, 99)),
+                                   "throughput_req_s": count / finish}}
+
+
 def run_kernels(args) -> dict:
     """The headline workload's two dominant kernels in their level-by-level
     launches (ARP_OPT_PIPELINE 0): the predictor's chain (one cluster launch
@@ -991,7 +1136,7 @@ def run_kernels(args) -> dict:
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
-    w = WORKLOAD
+    w = LARGE
     prec = b.ARP_FP32 if args.precision == "fp32" else b.ARP_FP64
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
@@ -1039,12 +1184,35 @@ def main():
         dist.init_process_group("nccl")
     out = run_ours(args, rank, world)
     if out is not None:
+        if world == 1 and not args.headline_only:
+            # the same solve on the single large instance, the time to 1e-5 and serving latency
+            big = run_ours(args, rank, world, LARGE, timed_steps=min(args.steps, 10))
+            out["config_N512"] = {k: big[k] for k in ("value", "unit", "ms_per_step", "config", "roofline", "e2e",
+                                                      "level_by_level", "fine_only", "clocks")}
+            tts = run_tts(args, LARGE)
+            out["tts"] = {"workload": tts["workload"], "target_rel_l2": tts["target"],
+                          "reference": tts["reference"],
+                          "fp32_bulk_solve_s": tts["fp32"]["seconds"], "fp32_k": tts["fp32"]["k_star"],
+                          "fp32_pipelined": tts["fp32"]["pipelined"], "fp32_error": tts["fp32"]["solve_error"],
+                          "fp64_plain_solve_s": tts["fp64"]["seconds"], "fp64_k": tts["fp64"]["k_star"],
+                          "fp64_error": tts["fp64"]["solve_error"],
+                          "speedup_fp32_vs_fp64": tts.get("speedup_fp32_vs_fp64"),
+                          "note": "end to end through the C ABI with host buffers, one instance each"}
+            out["serve"] = serve_one_rate()
         if world == 1 and not args.no_cpu_baseline:
-            dt, units = oracle_iteration_sample(CPU_SAMPLE_SLICES)
+            U = oracle_predictor(CPU_SAMPLE_SLICES)
+            dt, units = oracle_iteration_sample(CPU_SAMPLE_SLICES, WORKLOAD, U)
+            cores = host_cores()
+            dtp, unitsp, slp = oracle_iteration_parallel(cores, CPU_PARALLEL_SLICES_PER_CORE)
             out["cpu_baseline"] = {"value": units / dt, "unit": "grid-pt-steps/s", "cores": cpu_cores_used(),
-                                   "kind": "oracle",
+                                   "kind": "oracle", "cpu": cpu_model(),
                                    "sample": f"one FP64 oracle parareal iteration on {CPU_SAMPLE_SLICES} of "
-                                             f"{WORKLOAD.slices} slices ({dt:.1f} s)"}
+                                             f"{WORKLOAD.slices} slices ({dt:.1f} s), one core",
+                                   "parallel": {"value": unitsp / dtp, "unit": "grid-pt-steps/s", "cores": cores,
+                                                "sample": f"one FP64 oracle parareal iteration on {slp} of "
+                                                          f"{WORKLOAD.slices} slices ({dtp:.1f} s), F and G of "
+                                                          f"the slices in {cores} worker processes, the serial "
+                                                          "chain in one"}}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -61,11 +61,16 @@ typedef enum {
   ARP_TF32X3 = 2,       /* as ARP_FP32, but the real DFTs of the batched stages (the
                            ETDRK4 fine sweep, all states stepped together, and the
                            time average of arp_coarse_avg / arp_coarse_step) run as
-                           dense GEMMs on the tensor cores with TF32 operands split
-                           into high and low parts (three products, FP32
-                           accumulation); the serial coarse chain and the other fine
-                           schemes keep the FP32 FFT path */
-  ARP_BF16X2 = 3        /* as ARP_TF32X3 with BF16 high and low parts */
+                           dense GEMMs on the tensor cores (the library's own
+                           tcgen05 kernel) with TF32 operands split into high and
+                           low parts (three products, FP32 accumulation); the
+                           serial coarse chain and the other fine schemes keep the
+                           FP32 FFT path */
+  ARP_BF16X2 = 3,       /* as ARP_TF32X3 with BF16 high and low parts (all four
+                           products); about 16 significant bits per operand, so
+                           its results miss the 1e-5 FP32 bar on the time average */
+  ARP_BF16X3 = 4        /* as ARP_TF32X3 with BF16 high, middle and low parts (the
+                           six products of order <= 2) */
 } arp_precision;
 
 typedef enum {
@@ -316,6 +321,18 @@ arp_status arp_alu_peak(int precision, double* tflops, void* stream);
  * by level from u0, with the same result, and the context no longer pipelines.
  * ARP_EINVAL for NULL arguments. */
 arp_status arp_pipeline_info(const arp_ctx* ctx, int* out6);
+
+/* arp_gemm_check: the library's split-precision tensor-core GEMM (the
+ * contraction behind the DFT-as-GEMM precisions) on caller data, so it can be
+ * tested on its own: C[j][i] = sum_k A[i][k] B[j][k] for A (m x k), B (n x k)
+ * and C (n x m), all row-major FP32 device buffers owned by the caller;
+ * `precision` is ARP_TF32X3, ARP_BF16X2 or ARP_BF16X3 (how A and B are split
+ * into the MMA's input type).  Temporary operand buffers are allocated and
+ * freed inside the call, which synchronises `stream`.  The paper has no
+ * counterpart.  ARP_EINVAL for another precision, non-positive or too large
+ * sizes (m, k <= 65536) or NULL pointers; ARP_ENOMEM, ARP_ECUDA, or
+ * ARP_ETIMEOUT if a bounded wait of the kernel gave up. */
+arp_status arp_gemm_check(int precision, int m, int n, int k, const float* A, const float* B, float* C, void* stream);
 
 /* arp_chain_exchange_bytes: a host-side check of the cluster chain's byte
  * counts (no GPU work, no context).  For a grid of N points, a cluster of

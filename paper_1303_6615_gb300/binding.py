@@ -20,7 +20,7 @@ ARP_OK, ARP_EINVAL, ARP_ENOMEM, ARP_ECUDA, ARP_ETIMEOUT, ARP_ENONFINITE = range(
 ARP_FP64, ARP_FP32 = 0, 1
 ARP_OPT_T0, ARP_OPT_F, ARP_OPT_PRECISION, ARP_OPT_KMAX, ARP_OPT_TOL = 1, 2, 3, 4, 5
 ARP_OPT_CHAIN = 6
-ARP_TF32X3, ARP_BF16X2 = 2, 3
+ARP_TF32X3, ARP_BF16X2, ARP_BF16X3 = 2, 3, 4
 ARP_OPT_FINE_BLOCK = 7
 ARP_OPT_FINE_SCHEME = 8
 ARP_OPT_COARSE_SCHEME = 9
@@ -51,6 +51,7 @@ _SIGS = {
     "arp_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "arp_pipeline_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "arp_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
+    "arp_gemm_check": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "arp_chain_exchange_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_uint)]),
     "arp_coarse_avg_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P,
@@ -149,6 +150,17 @@ def arp_chain_exchange_bytes(N: int, cluster: int, rank: int, precision: int) ->
     if st != ARP_OK:
         raise ArpError(st, "arp_chain_exchange_bytes failed")
     return red.value, ws.value
+
+
+def arp_gemm_check(precision: int, A, B, C, stream=None) -> None:
+    """C[j][i] = sum_k A[i][k] B[j][k] on the split-precision tensor-core kernel;
+    A (m, k), B (n, k), C (n, m): contiguous float32 device tensors."""
+    m, k = A.shape
+    n = B.shape[0]
+    st = load_library().arp_gemm_check(precision, m, n, k, A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                                       _stream(stream))
+    if st != ARP_OK:
+        raise ArpError(st, "arp_gemm_check failed")
 
 
 def arp_pipeline_info(ctx: int) -> dict:

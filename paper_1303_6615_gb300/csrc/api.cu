@@ -181,7 +181,7 @@ using namespace arp;
 extern "C" {
 
 size_t arp_query_bytes(int N, int slices, int M, int precision) {
-  if (!pow2_in_range(N) || slices < 1 || M < 2 || precision < ARP_FP64 || precision > ARP_BF16X2) return 0;
+  if (!pow2_in_range(N) || slices < 1 || M < 2 || precision < ARP_FP64 || precision > ARP_BF16X3) return 0;
   Sizes z = sizes_of(N, slices, M);
   return z.tables + z.work + z.state;
 }
@@ -259,7 +259,8 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       c->tables_dirty = true;
       return ARP_OK;
     case ARP_OPT_PRECISION:
-      if (v != (double)ARP_FP64 && v != (double)ARP_FP32 && v != (double)ARP_TF32X3 && v != (double)ARP_BF16X2)
+      if (v != (double)ARP_FP64 && v != (double)ARP_FP32 && v != (double)ARP_TF32X3 && v != (double)ARP_BF16X2 &&
+          v != (double)ARP_BF16X3)
         return fail(c, ARP_EINVAL, "unknown precision");
       c->precision = (int)v;
       return ARP_OK;

@@ -1,6 +1,6 @@
 // dftgemm.cu -- the real DFTs of the nonlinearity as dense GEMMs on the tensor
-// cores (precisions ARP_TF32X3 and ARP_BF16X2): the evaluation of N for a batch
-// of states, used by the batched time average (one column group per
+// cores (precisions ARP_TF32X3, ARP_BF16X2 and ARP_BF16X3): the evaluation of N
+// for a batch of states, used by the batched time average (one column group per
 // (state, quadrature node)) and by a fine sweep that steps all slices in lock
 // step (one column group per slice and ETDRK4 stage).
 //
@@ -10,35 +10,43 @@
 //     c_r(p) = sum_j Wfwd[r][j] p(x_j), Wfwd = [cos(k x_j); -sin(k x_j)] / N          (R x N)
 // so the four inverse real transforms of a state (v1, h, v1_x, v2_x) are four
 // columns of X = Winv A and the three forward ones (the products) three columns
-// of Q = Wfwd P.  Both products are split-precision: every operand is split into
-// a high and a low part of the input type (TF32-rounded FP32, or BF16) and
-//     Winv A ~ Winv_hi A_hi + Winv_hi A_lo + Winv_lo A_hi,
-// accumulated in FP32 by cuBLAS (plain library GEMMs; all other steps run in the
-// kernels below).  The coefficient dimension is padded to Rp, a multiple of 8,
-// with zero rows and columns, so every operand column starts on a 16-byte
-// boundary (with R = 2K + 1 odd, the library would otherwise fall back to
-// element-aligned kernels).  The dense DFT costs 2 N R flops per column against the FFT's
-// ~2.5 N log2 N: this path exists for the precision study, not for speed.
-#include <cublas_v2.h>
-#include <cuda_bf16.h>
+// of Q = Wfwd P.  Both are split-precision products: every operand is split
+// into two or three parts of the input type (TF32-rounded FP32, or BF16) and
+//     Winv A ~ sum over the precision's products of Winv_part A_part,
+// accumulated in FP32 in tensor memory by the library's own tcgen05 kernel
+// (tc_gemm.cuh): the inverse GEMM's epilogue forms the products -v1 v1_x,
+// -v1 v2_x, -h v1 at every grid point from the accumulator and splits them
+// into the forward GEMM's operand, so X never reaches memory.  Packing, node
+// sums and the ETDRK4 combination run in the kernels below.  Both GEMMs keep
+// their operands K-major: Winv as [N][Rp], the coefficient columns as
+// [columns][Rp], Wfwd as [Rp][Nk], the products as [columns][Nk]; the
+// coefficient dimension is padded with zeros to Rp, a multiple of 128 (the
+// tile), and the grid dimension to Nk, a multiple of 64, so every TMA box lies
+// on a 16-byte boundary.  The dense DFT costs 2 N R flops per column against
+// the FFT's ~2.5 N log2 N: this path exists for the precision study and the
+// tensor-core measurement, not as the default.
+#include <cuda.h>
 
 #include <string>
 
 #include "context.h"
 #include "fine_impl.cuh"
+#include "tc_gemm.cuh"
 
 namespace arp {
 
 struct DftWork {
-  cublasHandle_t blas = nullptr;
-  int R = 0;               // padded coefficient rows: 2K + 1 rounded up to a multiple of 8
-  size_t cols = 0;         // column capacity of A and X (4 per state-node or slice)
-  void* Winv[2] = {nullptr, nullptr};
-  void* Wfwd[2] = {nullptr, nullptr};
-  void* A[2] = {nullptr, nullptr};
-  float* X = nullptr;
-  void* P[2] = {nullptr, nullptr};
-  float* Q = nullptr;
+  int R = 0;               // padded coefficient rows: 2K + 1 rounded up to a multiple of 128
+  int Mi = 0;              // padded rows of Winv: N rounded up to a multiple of 128
+  int Nk = 0;              // padded grid dimension of Wfwd and P: N rounded up to a multiple of 64
+  size_t cols = 0;         // column capacity of A (4 per column group)
+  void* Winv = nullptr;    // [parts][Mi][R]
+  void* Wfwd = nullptr;    // [parts][R][Nk]
+  void* A = nullptr;       // [parts][cols][R]
+  void* P = nullptr;       // [parts][3 cols / 4][Nk]
+  float* Q = nullptr;      // [3 cols / 4][R]
+  unsigned* status = nullptr;       // device: bit 0 set by a bounded wait that gave up
+  unsigned* status_host = nullptr;  // pinned copy read after each call
   int tables_prec = -1;    // precision the DFT matrices were split for
   // fine sweep state, [slices][3][K1] each
   int fine_cap = 0;
@@ -47,53 +55,46 @@ struct DftWork {
 
 namespace {
 
-struct SplitTF32 {
-  using E = float;
-  static constexpr cudaDataType_t kType = CUDA_R_32F;
-  static constexpr cublasComputeType_t kCompute = CUBLAS_COMPUTE_32F_FAST_TF32;
-  __device__ static void split(float x, E& hi, E& lo) {
-    unsigned h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    hi = __uint_as_float(h);
-    lo = x - hi;
-  }
-};
-
-struct SplitBF16 {
-  using E = __nv_bfloat16;
-  static constexpr cudaDataType_t kType = CUDA_R_16BF;
-  static constexpr cublasComputeType_t kCompute = CUBLAS_COMPUTE_32F;
-  __device__ static void split(float x, E& hi, E& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-  }
-};
+using tc::SplitBF16x2;
+using tc::SplitBF16x3;
+using tc::SplitTF32x3;
 
 template <class S>
-__global__ void dft_tables_kernel(int N, int K, int R, typename S::E* winv_hi, typename S::E* winv_lo,
-                                  typename S::E* wfwd_hi, typename S::E* wfwd_lo) {
+__global__ void dft_tables_kernel(int N, int K, int R, int Mi, int Nk, typename S::E* winv, typename S::E* wfwd) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)N * R) return;
-  const int j = (int)(t % N), r = (int)(t / N);
-  if (r > 2 * K) {  // padding
-    S::split(0.0f, winv_hi[j + (size_t)N * r], winv_lo[j + (size_t)N * r]);
-    S::split(0.0f, wfwd_hi[r + (size_t)R * j], wfwd_lo[r + (size_t)R * j]);
-    return;
+  const long long ni = (long long)Mi * R, nf = (long long)R * Nk;
+  if (t >= ni + nf) return;
+  int j, r;
+  typename S::E* dst;
+  size_t stride;
+  bool fwd = t >= ni;
+  if (!fwd) {
+    j = (int)(t / R);
+    r = (int)(t % R);
+    dst = winv + t;
+    stride = (size_t)ni;
+  } else {
+    r = (int)((t - ni) / Nk);
+    j = (int)((t - ni) % Nk);
+    dst = wfwd + (t - ni);
+    stride = (size_t)nf;
   }
-  const int k = r <= K ? r : r - K;
-  const long long m = ((long long)k * j) % N;  // exact argument reduction of k x_j
-  double sn, cs;
-  sincospi(2.0 * (double)m / (double)N, &sn, &cs);
-  const double vinv = r == 0 ? 1.0 : (r <= K ? 2.0 * cs : -2.0 * sn);
-  const double vfwd = (r == 0 ? 1.0 : (r <= K ? cs : -sn)) / (double)N;
-  S::split((float)vinv, winv_hi[j + (size_t)N * r], winv_lo[j + (size_t)N * r]);
-  S::split((float)vfwd, wfwd_hi[r + (size_t)R * j], wfwd_lo[r + (size_t)R * j]);
+  double v = 0.0;
+  if (j < N && r <= 2 * K) {
+    const int k = r <= K ? r : r - K;
+    const long long m = ((long long)k * j) % N;  // exact argument reduction of k x_j
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)N, &sn, &cs);
+    v = fwd ? (r == 0 ? 1.0 : (r <= K ? cs : -sn)) / (double)N : (r == 0 ? 1.0 : (r <= K ? 2.0 * cs : -2.0 * sn));
+  }
+  S::split_d(v, dst, stride);
 }
 
-// The four field columns of one state from its eigen amplitudes x (FP32) at k.
+// The four field columns of one state from its eigen amplitudes x (FP32) at k,
+// split into the parts of A ([parts][cols][R], parts `ps` elements apart).
 template <class S>
 __device__ __forceinline__ void pack_columns(const cf x[3], int k, int K, int R, float is, float ss, size_t g,
-                                             typename S::E* Ahi, typename S::E* Alo) {
+                                             typename S::E* A, size_t ps) {
   cf u[3];
   eigen_to_phys<float>(x, is, ss, u);
   const float kk = (float)k;
@@ -101,8 +102,8 @@ __device__ __forceinline__ void pack_columns(const cf x[3], int k, int K, int R,
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const size_t col = (4 * g + f) * (size_t)R;
-    S::split(F[f].x, Ahi[col + k], Alo[col + k]);
-    if (k > 0) S::split(F[f].y, Ahi[col + K + k], Alo[col + K + k]);
+    S::split(F[f].x, A + col + k, ps);
+    if (k > 0) S::split(F[f].y, A + col + K + k, ps);
   }
 }
 
@@ -110,7 +111,7 @@ __device__ __forceinline__ void pack_columns(const cf x[3], int k, int K, int R,
 template <class S>
 __global__ void dft_pack_avg_kernel(const cd* __restrict__ W, int nb, int M, int K, int R, const cf* __restrict__ ph,
                                     const float* __restrict__ is, const float* __restrict__ ss,
-                                    typename S::E* Ahi, typename S::E* Alo) {
+                                    typename S::E* A, size_t ps) {
   const int K1 = K + 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nb * M * K1) return;
@@ -120,13 +121,13 @@ __global__ void dft_pack_avg_kernel(const cd* __restrict__ W, int nb, int M, int
   cf x[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) x[b] = ph[((size_t)m * 3 + b) * K1 + k] * cvt<float>(W[((size_t)s * 3 + b) * K1 + k]);
-  pack_columns<S>(x, k, K, R, is[k], ss[k], g, Ahi, Alo);
+  pack_columns<S>(x, k, K, R, is[k], ss[k], g, A, ps);
 }
 
 // Column groups (slice s): the fine sweep's stage inputs.
 template <class S>
 __global__ void dft_pack_fine_kernel(const cf* __restrict__ X, int S_, int K, int R, const float* __restrict__ is,
-                                     const float* __restrict__ ss, typename S::E* Ahi, typename S::E* Alo) {
+                                     const float* __restrict__ ss, typename S::E* A, size_t ps) {
   const int K1 = K + 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)S_ * K1) return;
@@ -135,22 +136,7 @@ __global__ void dft_pack_fine_kernel(const cf* __restrict__ X, int S_, int K, in
   cf x[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) x[b] = X[(g * 3 + b) * K1 + k];
-  pack_columns<S>(x, k, K, R, is[k], ss[k], g, Ahi, Alo);
-}
-
-// Products at the samples of each column group: -v1 v1_x, -v1 v2_x, -h v1.
-template <class S>
-__global__ void dft_products_kernel(const float* __restrict__ X, int N, long long groups, typename S::E* Phi,
-                                    typename S::E* Plo) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= groups * N) return;
-  const int j = (int)(t % N);
-  const size_t g = (size_t)(t / N);
-  const float v1 = X[j + (size_t)N * (4 * g)], h = X[j + (size_t)N * (4 * g + 1)];
-  const float v1x = X[j + (size_t)N * (4 * g + 2)], v2x = X[j + (size_t)N * (4 * g + 3)];
-  const float p[3] = {-v1 * v1x, -v1 * v2x, -h * v1};
-#pragma unroll
-  for (int f = 0; f < 3; ++f) S::split(p[f], Phi[j + (size_t)N * (3 * g + f)], Plo[j + (size_t)N * (3 * g + f)]);
+  pack_columns<S>(x, k, K, R, is[k], ss[k], g, A, ps);
 }
 
 // b = R^H (P1, P2, i k P3) of column group g at k from the forward coefficients.
@@ -267,27 +253,66 @@ __global__ void dft_fine_store_kernel(cd* __restrict__ out, int S_, int H, int K
 
 unsigned blocks_for(long long n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
-arp_status blas_check(arp_ctx* c, cublasStatus_t st, const char* what) {
-  if (st == CUBLAS_STATUS_SUCCESS) return ARP_OK;
-  return fail(c, st == CUBLAS_STATUS_ALLOC_FAILED ? ARP_ENOMEM : ARP_ECUDA,
-              std::string(what) + ": cuBLAS status " + std::to_string((int)st));
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
+// does not link the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
 }
 
-// C (m x n, FP32) = A B with A (m x k) and B (k x n) given as hi/lo parts:
-// A_hi B_hi + A_hi B_lo + A_lo B_hi, column-major.
+// Tensor map of a K-major operand [parts][rows_alloc][kdim] of which the first
+// `rows` rows are read, with 128 x (128-byte) boxes, 128-byte swizzle, zero
+// fill beyond `rows`.
 template <class S>
-arp_status gemm3(arp_ctx* c, cublasHandle_t h, int m, int n, int k, void* const A[2], int lda, void* const B[2],
-                 int ldb, float* C, int ldc) {
-  const float one = 1.0f, zero = 0.0f;
-  const void* ops[3][2] = {{A[0], B[0]}, {A[0], B[1]}, {A[1], B[0]}};
-  for (int i = 0; i < 3; ++i) {
-    const cublasStatus_t st =
-        cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, ops[i][0], S::kType, lda, ops[i][1], S::kType, ldb,
-                     i == 0 ? &zero : &one, C, CUDA_R_32F, ldc, S::kCompute, CUBLAS_GEMM_DEFAULT);
-    arp_status r = blas_check(c, st, "dft gemm");
-    if (r != ARP_OK) return r;
-  }
+arp_status make_map(arp_ctx* c, CUtensorMap* map, void* base, int kdim, long long rows, long long rows_alloc) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(c, ARP_ECUDA, "dft: cuTensorMapEncodeTiled is unavailable");
+  const cuuint64_t es = sizeof(typename S::E);
+  const cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)S::kParts};
+  const cuuint64_t strides[2] = {(cuuint64_t)kdim * es, (cuuint64_t)kdim * es * (cuuint64_t)rows_alloc};
+  const cuuint32_t box[3] = {(cuuint32_t)(tc::kRowBytes / es), (cuuint32_t)tc::kBM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(map, S::kMapType, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, ARP_ECUDA, "dft: tensor map (CUresult " + std::to_string((int)r) + ")");
   return ARP_OK;
+}
+
+// One split-precision GEMM on the tensor cores: tiles of 128 x 128 over
+// (m_rows, ncols), blockIdx.x over row tiles so the CTAs that share a column
+// tile of B run together.
+template <class S, int EPI>
+arp_status tc_gemm(arp_ctx* c, void* A, int m_rows, void* B, long long ncols, long long b_rows_alloc, int kdim,
+                   const tc::Epilogue& ep, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  arp_status r;
+  if ((r = make_map<S>(c, &ma, A, kdim, m_rows, m_rows)) != ARP_OK) return r;
+  if ((r = make_map<S>(c, &mb, B, kdim, ncols, b_rows_alloc)) != ARP_OK) return r;
+  const void* kern = (const void*)tc::split_gemm_kernel<S, EPI>;
+  const size_t smem = tc::smem_bytes<S>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return check_cuda(c, e, "dft gemm: shared-memory attribute");
+  const long long ntiles = (ncols + tc::kBN - 1) / tc::kBN;
+  if (ntiles > 65535) return fail(c, ARP_EINVAL, "dft gemm: too many column tiles in one pass");
+  const int kblocks = kdim / (tc::kRowBytes / (int)sizeof(typename S::E));
+  tc::Epilogue epc = ep;
+  void* args[] = {(void*)&ma, (void*)&mb, (void*)&kblocks, (void*)&epc};
+  e = cudaLaunchKernel(kern, dim3(m_rows / tc::kBM, (unsigned)ntiles), dim3(tc::kThreads), args, smem, s);
+  return check_cuda(c, e, "dft gemm: launch");
 }
 
 template <class S>
@@ -302,14 +327,19 @@ arp_status ensure_work(arp_ctx* c, size_t cols, int fine, cudaStream_t s) {
   if (!d) {
     d = new (std::nothrow) DftWork();
     if (!d) return fail(c, ARP_ENOMEM, "dft: host allocation");
-    if (cublasCreate(&d->blas) != CUBLAS_STATUS_SUCCESS) {
-      d->blas = nullptr;
-      return fail(c, ARP_ECUDA, "dft: cuBLAS handle");
+    d->R = (2 * c->K + 1 + 127) / 128 * 128;
+    d->Mi = (c->N + 127) / 128 * 128;
+    d->Nk = (c->N + 63) / 64 * 64;
+    if (cudaMalloc(&d->status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&d->status_host, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, ARP_ENOMEM, "dft: status word");
     }
-    d->R = (2 * c->K + 1 + 7) / 8 * 8;
+    if (cudaMemsetAsync(d->status, 0, sizeof(unsigned), s) != cudaSuccess)
+      return check_cuda(c, cudaGetLastError(), "dft: status word");
   }
-  const int N = c->N, R = d->R;
-  const size_t eb = elem_bytes<S>();
+  const int R = d->R, Mi = d->Mi, Nk = d->Nk;
+  const size_t eb = elem_bytes<S>(), parts = S::kParts;
   auto grow = [&](void*& p, size_t bytes) -> arp_status {
     if (p) cudaFree(p);
     p = nullptr;
@@ -323,27 +353,24 @@ arp_status ensure_work(arp_ctx* c, size_t cols, int fine, cudaStream_t s) {
   };
   arp_status r;
   if (d->tables_prec != c->precision) {
-    for (int i = 0; i < 2; ++i) {
-      if ((r = grow(d->Winv[i], (size_t)N * R * eb)) != ARP_OK) return r;
-      if ((r = grow(d->Wfwd[i], (size_t)N * R * eb)) != ARP_OK) return r;
-    }
+    if ((r = grow(d->Winv, parts * Mi * R * eb)) != ARP_OK) return r;
+    if ((r = grow(d->Wfwd, parts * R * Nk * eb)) != ARP_OK) return r;
     using E = typename S::E;
-    dft_tables_kernel<S><<<blocks_for((long long)N * R, 256), 256, 0, s>>>(
-        N, c->K, R, (E*)d->Winv[0], (E*)d->Winv[1], (E*)d->Wfwd[0], (E*)d->Wfwd[1]);
+    dft_tables_kernel<S><<<blocks_for((long long)Mi * R + (long long)R * Nk, 256), 256, 0, s>>>(
+        c->N, c->K, R, Mi, Nk, (E*)d->Winv, (E*)d->Wfwd);
     if ((r = check_cuda(c, cudaGetLastError(), "dft: tables")) != ARP_OK) return r;
     d->tables_prec = c->precision;
     d->cols = 0;  // the element type of the operands changed
   }
   if (cols > d->cols) {
-    for (int i = 0; i < 2; ++i) {
-      if ((r = grow(d->A[i], cols * R * eb)) != ARP_OK) return r;
-      // the padding rows of A are never written: zero (a zero bit pattern in both types)
-      if ((r = check_cuda(c, cudaMemsetAsync(d->A[i], 0, cols * R * eb, s), "dft: workspace")) != ARP_OK) return r;
-      if ((r = grow(d->P[i], cols / 4 * 3 * N * eb)) != ARP_OK) return r;
-    }
-    void* x = d->X;
-    if ((r = grow(x, cols * N * sizeof(float))) != ARP_OK) return r;
-    d->X = (float*)x;
+    // padding rows of A and padding points of P are never written: zero (a zero
+    // bit pattern in both input types)
+    if ((r = grow(d->A, parts * cols * R * eb)) != ARP_OK) return r;
+    if ((r = check_cuda(c, cudaMemsetAsync(d->A, 0, parts * cols * R * eb, s), "dft: workspace")) != ARP_OK) return r;
+    if ((r = grow(d->P, parts * (cols / 4 * 3) * Nk * eb)) != ARP_OK) return r;
+    if ((r = check_cuda(c, cudaMemsetAsync(d->P, 0, parts * (cols / 4 * 3) * Nk * eb, s), "dft: workspace")) !=
+        ARP_OK)
+      return r;
     void* q = d->Q;
     if ((r = grow(q, cols / 4 * 3 * R * sizeof(float))) != ARP_OK) return r;
     d->Q = (float*)q;
@@ -358,21 +385,37 @@ arp_status ensure_work(arp_ctx* c, size_t cols, int fine, cudaStream_t s) {
     }
     d->fine_cap = fine;
   }
-  if (cublasSetStream(d->blas, s) != CUBLAS_STATUS_SUCCESS) return fail(c, ARP_ECUDA, "dft: cuBLAS stream");
   return ARP_OK;
 }
 
-// X = Winv A for `groups` column groups, then P = products, then Q = Wfwd P.
+// The inverse GEMM X = Winv A for `groups` column groups with the products
+// formed in its epilogue (P), then Q = Wfwd P.
 template <class S>
 arp_status dft_transforms(arp_ctx* c, long long groups, cudaStream_t s) {
   DftWork* d = c->dft;
   const int N = c->N, R = d->R;
+  const long long cols = 4 * groups, cols3 = 3 * groups;
+  tc::Epilogue ei{nullptr, d->P, cols, 0, d->Nk, (long long)(d->cols / 4 * 3) * d->Nk, N, d->status};
+  arp_status r = tc_gemm<S, tc::kEpiProducts>(c, d->Winv, d->Mi, d->A, cols, (long long)d->cols, R, ei, s);
+  if (r != ARP_OK) return r;
+  tc::Epilogue ef{d->Q, nullptr, cols3, R, 0, 0, R, d->status};
+  return tc_gemm<S, tc::kEpiStore>(c, d->Wfwd, R, d->P, cols3, (long long)(d->cols / 4 * 3), d->Nk, ef, s);
+}
+
+// After the last GEMM of a call: the bounded waits' status word, read back
+// (the call's stream is synchronised) and cleared.
+arp_status dft_status(arp_ctx* c, cudaStream_t s) {
+  DftWork* d = c->dft;
   arp_status r;
-  if ((r = gemm3<S>(c, d->blas, N, (int)(4 * groups), R, d->Winv, N, d->A, R, d->X, N)) != ARP_OK) return r;
-  using E = typename S::E;
-  dft_products_kernel<S><<<blocks_for(groups * N, 256), 256, 0, s>>>(d->X, N, groups, (E*)d->P[0], (E*)d->P[1]);
-  if ((r = check_cuda(c, cudaGetLastError(), "dft: products")) != ARP_OK) return r;
-  return gemm3<S>(c, d->blas, R, (int)(3 * groups), N, d->Wfwd, R, d->P, N, d->Q, R);
+  if ((r = check_cuda(c, cudaMemcpyAsync(d->status_host, d->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                      "dft: status read")) != ARP_OK ||
+      (r = check_cuda(c, cudaStreamSynchronize(s), "dft: synchronise")) != ARP_OK)
+    return r;
+  if (*d->status_host != 0u) {
+    cudaMemsetAsync(d->status, 0, sizeof(unsigned), s);
+    return fail(c, ARP_ETIMEOUT, "dft gemm: a bounded wait of the tensor-core kernel gave up");
+  }
+  return ARP_OK;
 }
 
 template <class S>
@@ -388,15 +431,15 @@ arp_status dft_nbar_t(arp_ctx* c, const cd* W, cd* partial, int batch, cudaStrea
     const int nb = batch - s0 < per ? batch - s0 : per;
     const long long groups = (long long)nb * M;
     dft_pack_avg_kernel<S><<<blocks_for(groups * K1, 128), 128, 0, s>>>(
-        W + (size_t)s0 * 3 * K1, nb, M, c->K, d->R, c->phase32, c->inv_sig32, c->sk_sig32, (E*)d->A[0],
-        (E*)d->A[1]);
+        W + (size_t)s0 * 3 * K1, nb, M, c->K, d->R, c->phase32, c->inv_sig32, c->sk_sig32, (E*)d->A,
+        d->cols * (size_t)d->R);
     if ((r = check_cuda(c, cudaGetLastError(), "dft: pack")) != ARP_OK) return r;
     if ((r = dft_transforms<S>(c, groups, s)) != ARP_OK) return r;
     dft_unpack_avg_kernel<<<dim3((K1 + 31) / 32, nb), dim3(32, kAvgChunks), 0, s>>>(
         d->Q, nb, M, c->K, d->R, c->phase32, c->weight32, c->inv_sig32, c->sk_sig32, partial + (size_t)s0 * 3 * K1);
     if ((r = check_cuda(c, cudaGetLastError(), "dft: unpack")) != ARP_OK) return r;
   }
-  return ARP_OK;
+  return dft_status(c, s);
 }
 
 template <class S>
@@ -412,7 +455,7 @@ arp_status dft_fine_t(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t
   for (int step = 0; step < c->steps; ++step) {
     for (int stage = 0; stage < 4; ++stage) {
       dft_pack_fine_kernel<S><<<blocks_for(n, 128), 128, 0, s>>>(d->XS, batch, c->K, d->R, c->inv_sig32,
-                                                                  c->sk_sig32, (E*)d->A[0], (E*)d->A[1]);
+                                                                  c->sk_sig32, (E*)d->A, d->cols * (size_t)d->R);
       if ((r = check_cuda(c, cudaGetLastError(), "dft fine: pack")) != ARP_OK) return r;
       if ((r = dft_transforms<S>(c, batch, s)) != ARP_OK) return r;
       dft_fine_stage_kernel<<<blocks_for(n, 128), 128, 0, s>>>(d->Q, batch, c->K, d->R, stage, tb, d->U, d->ULO,
@@ -422,35 +465,112 @@ arp_status dft_fine_t(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t
   }
   dft_fine_store_kernel<<<blocks_for((long long)batch * c->H, 128), 128, 0, s>>>(out, batch, c->H, c->K, tb, d->U,
                                                                                   d->ULO);
-  return check_cuda(c, cudaGetLastError(), "dft fine: store");
+  if ((r = check_cuda(c, cudaGetLastError(), "dft fine: store")) != ARP_OK) return r;
+  return dft_status(c, s);
+}
+
+template <class S>
+__global__ void split_rows_kernel(const float* __restrict__ X, long long rows, int cols, int ld,
+                                  typename S::E* out, size_t part_stride) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * ld) return;
+  const long long r = t / ld;
+  const int k = (int)(t % ld);
+  S::split(k < cols ? X[r * cols + k] : 0.0f, out + t, part_stride);
+}
+
+// C (n x m, row-major FP32), C[j][i] = sum_k A[i][k] B[j][k], with A (m x k)
+// and B (n x k) row-major FP32, through the split-precision tensor-core kernel
+// (operands split and padded in temporary device buffers).
+template <class S>
+arp_status gemm_check_t(arp_ctx* c, int m, int n, int k, const float* A, const float* B, float* C, cudaStream_t s) {
+  const int mp = (m + tc::kBM - 1) / tc::kBM * tc::kBM;
+  const int ke = tc::kRowBytes / (int)sizeof(typename S::E);
+  const int kp = (k + ke - 1) / ke * ke;
+  const size_t eb = sizeof(typename S::E);
+  void *a = nullptr, *b = nullptr;
+  unsigned* st = nullptr;
+  float* ct = nullptr;
+  arp_status r = ARP_OK;
+  if (cudaMalloc(&a, (size_t)S::kParts * mp * kp * eb) != cudaSuccess ||
+      cudaMalloc(&b, (size_t)S::kParts * n * kp * eb) != cudaSuccess ||
+      cudaMalloc(&ct, (size_t)n * mp * sizeof(float)) != cudaSuccess || cudaMalloc(&st, sizeof(unsigned)) != cudaSuccess)
+    r = fail(c, ARP_ENOMEM, "gemm check: allocation");
+  if (r == ARP_OK) r = check_cuda(c, cudaMemsetAsync(a, 0, (size_t)S::kParts * mp * kp * eb, s), "gemm check");
+  if (r == ARP_OK) r = check_cuda(c, cudaMemsetAsync(st, 0, sizeof(unsigned), s), "gemm check");
+  if (r == ARP_OK) {
+    split_rows_kernel<S><<<blocks_for((long long)m * kp, 256), 256, 0, s>>>(A, m, k, kp, (typename S::E*)a,
+                                                                             (size_t)mp * kp);
+    split_rows_kernel<S><<<blocks_for((long long)n * kp, 256), 256, 0, s>>>(B, n, k, kp, (typename S::E*)b,
+                                                                             (size_t)n * kp);
+    r = check_cuda(c, cudaGetLastError(), "gemm check: split");
+  }
+  // the kernel stores C^T column-major: ct[col * mp + row] = C[row][col]
+  if (r == ARP_OK) r = tc_gemm<S, tc::kEpiStore>(c, a, mp, b, n, n, kp,
+                                                tc::Epilogue{ct, nullptr, n, mp, 0, 0, m, st}, s);
+  if (r == ARP_OK)
+    r = check_cuda(c, cudaMemcpy2DAsync(C, (size_t)m * sizeof(float), ct, (size_t)mp * sizeof(float),
+                                        (size_t)m * sizeof(float), (size_t)n, cudaMemcpyDeviceToDevice, s),
+                   "gemm check: copy");
+  unsigned hs = 0;
+  if (r == ARP_OK) r = check_cuda(c, cudaMemcpyAsync(&hs, st, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "gemm check");
+  if (r == ARP_OK) r = check_cuda(c, cudaStreamSynchronize(s), "gemm check: synchronise");
+  if (r == ARP_OK && hs) r = fail(c, ARP_ETIMEOUT, "gemm check: a bounded wait gave up");
+  cudaFree(a);
+  cudaFree(b);
+  cudaFree(ct);
+  cudaFree(st);
+  return r;
 }
 
 }  // namespace
 
-bool dft_mode(const arp_ctx* c) { return c->precision == ARP_TF32X3 || c->precision == ARP_BF16X2; }
+bool dft_mode(const arp_ctx* c) {
+  return c->precision == ARP_TF32X3 || c->precision == ARP_BF16X2 || c->precision == ARP_BF16X3;
+}
 
 arp_status dft_nbar(arp_ctx* c, const cd* W, cd* partial, int batch, cudaStream_t s) {
   if (batch == 0) return ARP_OK;
-  return c->precision == ARP_BF16X2 ? dft_nbar_t<SplitBF16>(c, W, partial, batch, s)
-                                    : dft_nbar_t<SplitTF32>(c, W, partial, batch, s);
+  switch (c->precision) {
+    case ARP_BF16X2: return dft_nbar_t<SplitBF16x2>(c, W, partial, batch, s);
+    case ARP_BF16X3: return dft_nbar_t<SplitBF16x3>(c, W, partial, batch, s);
+    default: return dft_nbar_t<SplitTF32x3>(c, W, partial, batch, s);
+  }
 }
 
 arp_status dft_fine(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
   if (batch == 0) return ARP_OK;
-  return c->precision == ARP_BF16X2 ? dft_fine_t<SplitBF16>(c, in, out, batch, s)
-                                    : dft_fine_t<SplitTF32>(c, in, out, batch, s);
+  switch (c->precision) {
+    case ARP_BF16X2: return dft_fine_t<SplitBF16x2>(c, in, out, batch, s);
+    case ARP_BF16X3: return dft_fine_t<SplitBF16x3>(c, in, out, batch, s);
+    default: return dft_fine_t<SplitTF32x3>(c, in, out, batch, s);
+  }
 }
 
 void dft_release(arp_ctx* c) {
   DftWork* d = c->dft;
   if (!d) return;
-  void* ptrs[] = {d->Winv[0], d->Winv[1], d->Wfwd[0], d->Wfwd[1], d->A[0], d->A[1], d->X, d->P[0], d->P[1], d->Q,
-                  d->U, d->ULO, d->NU, d->A1, d->ACC, d->XS};
+  void* ptrs[] = {d->Winv, d->Wfwd, d->A, d->P, d->Q, d->U, d->ULO, d->NU, d->A1, d->ACC, d->XS, d->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (d->blas) cublasDestroy(d->blas);
+  if (d->status_host) cudaFreeHost(d->status_host);
   delete d;
   c->dft = nullptr;
 }
 
 }  // namespace arp
+
+extern "C" arp_status arp_gemm_check(int precision, int m, int n, int k, const float* A, const float* B, float* C,
+                                     void* stream) {
+  using namespace arp;
+  if (m < 1 || n < 1 || k < 1 || m > (1 << 16) || n > (1 << 22) || k > (1 << 16) || !A || !B || !C) return ARP_EINVAL;
+  if ((long long)(n + tc::kBN - 1) / tc::kBN > 65535) return ARP_EINVAL;
+  arp_ctx c;  // host-side error record only
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (precision) {
+    case ARP_TF32X3: return gemm_check_t<SplitTF32x3>(&c, m, n, k, A, B, C, s);
+    case ARP_BF16X2: return gemm_check_t<SplitBF16x2>(&c, m, n, k, A, B, C, s);
+    case ARP_BF16X3: return gemm_check_t<SplitBF16x3>(&c, m, n, k, A, B, C, s);
+    default: return ARP_EINVAL;
+  }
+}

@@ -63,7 +63,11 @@ constexpr int kSchemeIfrk4 = 1;
 
 template <int LOGN> struct FineBlock {
   static constexpr int N = 1 << LOGN;
+#ifdef ARP_FINE_EIGHTH
+  static constexpr int value = LOGN >= 10 ? N / 8 : (N / 4 < 32 ? 32 : (N / 4 > 512 ? 512 : N / 4));
+#else
   static constexpr int value = N / 4 < 32 ? 32 : (N / 4 > 512 ? 512 : N / 4);
+#endif
 };
 
 // Second block size of the FP32 fine sweep: N/2 threads (at most 512).
@@ -277,7 +281,13 @@ template <int LOGN, int BLOCK>
 struct F32Layout {
   static constexpr int K1 = ((1 << LOGN) - 1) / 3 + 1;
   static constexpr int kMPT = (K1 + BLOCK - 1) / BLOCK;
-  static constexpr size_t kBytes = (size_t)lanes_and_twiddles<float>(LOGN) * sizeof(cf) + (size_t)2 * K1 * sizeof(float);
+#ifdef ARP_FINE_SMEM_STATE
+  static constexpr bool kSmemState = LOGN >= 10 && BLOCK * 8 == (1 << LOGN);
+#else
+  static constexpr bool kSmemState = false;
+#endif
+  static constexpr size_t kBytes = (size_t)lanes_and_twiddles<float>(LOGN) * sizeof(cf) +
+                                   (size_t)2 * K1 * sizeof(float) + (kSmemState ? (size_t)9 * K1 * sizeof(cf) : 0);
 };
 
 // One ETDRK4 stage of the FP32 path for one (wavenumber, branch) entry i of the
@@ -323,6 +333,8 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
   cf* TW = Z1 + padded_len<T>(N);
   T* IS = reinterpret_cast<T*>(TW + twiddle_count(LOGN));
   T* SS = IS + K1;
+  constexpr bool kSmemState = F32Layout<LOGN, BLOCK>::kSmemState && SCHEME == kSchemeEtdrk4;
+  cf* NUS = reinterpret_cast<cf*>(SS + K1);  // kSmemState: N(u), a1, acc in shared memory, [3][3][K1]
 
   cf u[MPT][3], ulo[MPT][3], nu[MPT][3], a1[MPT][3], acc[MPT][3], acclo[MPT][3];
   const cd* src = in + (size_t)slice * 3 * H;
@@ -354,7 +366,11 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
     const bool last = (step == steps - 1);
 #pragma unroll 1
     for (int stage = 0; stage < 4; ++stage) {
+#ifdef ARP_FINE_PAIRS
+      nonlinear_transform_pairs<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
+#else
       nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
+#endif
       const bool pack_next = !(last && stage == 3);
 #pragma unroll
       for (int r = 0; r < MPT; ++r) {
@@ -391,6 +407,9 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
               acclo[r][q] = mk<float>(re.lo, im.lo);
               nx[q] = (stage == 1) ? E2 * u[r][q] + (0.5f * h) * bn[q] : ldgc(e.E + i) * u[r][q] + h * w;
             }
+          } else if constexpr (kSmemState) {
+            nx[q] = etd32_stage(stage, i, bn[q], u[r][q], ulo[r][q], NUS[i], NUS[3 * K1 + i], NUS[6 * K1 + i], e,
+                                tb.E_lo);
           } else {
             nx[q] = etd32_stage(stage, i, bn[q], u[r][q], ulo[r][q], nu[r][q], a1[r][q], acc[r][q], e, tb.E_lo);
           }
@@ -421,8 +440,15 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
   }
 }
 
+#if defined(ARP_FINE_SMEM_STATE)
+#define ARP_F32_BOUNDS __launch_bounds__(BLOCK, (BLOCK >= 256 ? 65536 / (BLOCK * 128) : (F32Layout<LOGN, BLOCK>::kSmemState ? 4 : 1)))
+#elif defined(ARP_FINE_PAIRS)
+#define ARP_F32_BOUNDS __launch_bounds__(BLOCK, (BLOCK >= 256 ? 65536 / (BLOCK * 128) : 1))
+#else
+#define ARP_F32_BOUNDS __launch_bounds__(BLOCK)
+#endif
 template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
-__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
+__global__ void ARP_F32_BOUNDS fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
                                                                int steps, FineTabs<float> tb) {
   fine_f32_body<LOGN, BLOCK, SCHEME>(in, out, steps, tb, blockIdx.x);
 }
@@ -453,6 +479,13 @@ arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int s
   else kern = (const void*)fine_sweep_kernel<T, LOGN, BLOCK, SCHEME>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");
+  if constexpr (kF32) {
+    if (F32Layout<LOGN, BLOCK>::kSmemState) {
+      // four such blocks per SM need the largest shared-memory carveout
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory carveout");
+    }
+  }
   FineTabs<T> tb = fine_tabs<T>(c);
   void* args[] = {(void*)&in, (void*)&out, &steps, &tb};
   e = cudaLaunchKernel(kern, dim3(batch), dim3(BLOCK), args, smem, s);

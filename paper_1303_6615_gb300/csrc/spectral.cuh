@@ -275,6 +275,68 @@ __device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>
   }
 }
 
+// radix8_stage on both lanes of `npairs` lane pairs at once: one item is the
+// butterfly at the same positions of lanes 2p and 2p+1, so the positions and
+// twiddles are computed and loaded once for the two lanes and the thread runs
+// two independent DFTs.  PRUNE 2 (last forward stage) also skips lane 2p+1's
+// outputs q = 5..7: only its bins k <= K < 3N/8 are ever read (the third
+// field's spectrum), while lane 2p needs bins k and N-k.  Arithmetic per lane
+// as radix8_stage.
+template <typename T, int N, int BLOCK, int SIGN, bool DIF, int PRUNE = 0>
+__device__ __forceinline__ void radix8_stage_pairs(cpx<T>* Z, int npairs, const cpx<T>* tw, int logL) {
+  constexpr int PL = padded_len<T>(N);
+  constexpr int NB = N / 8;
+  const int e = 1 << (logL - 3);
+  for (int item = threadIdx.x; item < npairs * NB; item += BLOCK) {
+    const int pair = item / NB;
+    const int bidx = item - pair * NB;
+    cpx<T>* Z0 = Z + 2 * pair * PL;
+    cpx<T>* Z1 = Z0 + PL;
+    const int j = bidx & (e - 1);
+    const int base = ((bidx >> (logL - 3)) << logL) + j;
+    int at[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) at[q] = pidx<T, N>(base + q * e);
+    cpx<T> x[8], y[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (PRUNE == 1 && (q == 3 || q == 4)) continue;
+      x[q] = Z0[at[q]];
+      y[q] = Z1[at[q]];
+    }
+    if (!DIF && j) {
+#pragma unroll
+      for (int q = 1; q < 8; ++q) {
+        const cpx<T> w = tw[(q - 1) * e + j];
+        x[q] = x[q] * w;
+        y[q] = y[q] * w;
+      }
+    }
+    if (PRUNE == 1) {
+      dft8_in34zero<T, SIGN>(x);
+      dft8_in34zero<T, SIGN>(y);
+    } else {
+      dft8<T, SIGN>(x);
+      dft8<T, SIGN>(y);
+    }
+    if (DIF && j) {
+#pragma unroll
+      for (int q = 1; q < 8; ++q) {
+        const cpx<T> w = conj(tw[(q - 1) * e + j]);
+        x[q] = x[q] * w;
+        y[q] = y[q] * w;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (PRUNE == 2 && (q == 3 || q == 4)) continue;
+      Z0[at[q]] = x[q];
+      if (PRUNE == 2 && q > 4) continue;
+      Z1[at[q]] = y[q];
+    }
+  }
+}
+
 // Products at one physical sample: z0 = v1 + i h, z1 = v1_x + i v2_x.
 template <typename T>
 __device__ __forceinline__ void products(cpx<T>& z0, cpx<T>& z1) {
@@ -360,6 +422,34 @@ __device__ __forceinline__ void nonlinear_transform(cpx<T>* Z, int nstates, cons
   if constexpr (LOGN > LOGMID) {
     // span N last: bins 3N/8 .. 5N/8-1 lie above the kept modes and are not read
     radix8_stage<T, N, BLOCK, -1, false, 2>(Z, 2 * nstates, TW + twiddle_offset(LOGN, LOGN), LOGN);
+    __syncthreads();
+  }
+}
+
+// nonlinear_transform with both lanes of a state in one butterfly item
+// (radix8_stage_pairs): N/8 items per outer stage instead of N/4.
+template <typename T, int LOGN, int BLOCK>
+__device__ __forceinline__ void nonlinear_transform_pairs(cpx<T>* Z, int nstates, const cpx<T>* TW) {
+  constexpr int N = 1 << LOGN;
+  constexpr int LOGMID = stage_log_mid(LOGN);
+  if constexpr (LOGN > LOGMID) {
+    radix8_stage_pairs<T, N, BLOCK, +1, true, 1>(Z, nstates, TW + twiddle_offset(LOGN, LOGN), LOGN);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int logL = LOGN - 3; logL > LOGMID; logL -= 3) {
+    radix8_stage_pairs<T, N, BLOCK, +1, true>(Z, nstates, TW + twiddle_offset(LOGN, logL), logL);
+    __syncthreads();
+  }
+  middle_stage<T, LOGN, BLOCK>(Z, nstates);
+  __syncthreads();
+#pragma unroll
+  for (int logL = LOGMID + 3; logL < LOGN; logL += 3) {
+    radix8_stage_pairs<T, N, BLOCK, -1, false>(Z, nstates, TW + twiddle_offset(LOGN, logL), logL);
+    __syncthreads();
+  }
+  if constexpr (LOGN > LOGMID) {
+    radix8_stage_pairs<T, N, BLOCK, -1, false, 2>(Z, nstates, TW + twiddle_offset(LOGN, LOGN), LOGN);
     __syncthreads();
   }
 }
