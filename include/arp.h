@@ -85,10 +85,13 @@ typedef enum {
                               first), 1 =
                               cooperative grid, 2 = launches, 3 = the cluster only; all give
                               the same result up to rounding (default 0) */
-  ARP_OPT_FINE_BLOCK = 7,  /* FP32 fine sweep threads per slice: 0 = the default for the grid
-                              size (the faster on GB300), 1 = N/4, 2 = N/2 (both at least 32,
-                              at most 512); both are within the FP32 error bound, their results
-                              differ in the last bits (default 0) */
+  ARP_OPT_FINE_BLOCK = 7,  /* FP32 fine sweep schedule: 0 = the tuned default for the grid size
+                              (chosen offline from GB300 timings), 1 = N/4 threads per slice,
+                              2 = N/2 threads (both at least 32, at most 512), 3 = N/8 threads
+                              with both FFT lanes per butterfly and the ETDRK4 stage values in
+                              shared memory (ETDRK4, N >= 256; elsewhere the default applies);
+                              all are within the FP32 error bound, their results differ in the
+                              last bits (default 0) */
   ARP_OPT_FINE_SCHEME = 8,  /* fine propagator F: 0 = ETDRK4 (Cox & Matthews, default), 1 = Strang
                                splitting (Algorithm 3: exact linear half steps around a midpoint
                                step of N), 2 = integrating-factor RK4 (classical RK4 on

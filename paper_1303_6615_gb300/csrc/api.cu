@@ -302,7 +302,8 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       c->pipeline = (int)v;
       return ARP_OK;
     case ARP_OPT_FINE_BLOCK:
-      if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1 or 2");
+      if (v != 0.0 && v != 1.0 && v != 2.0 && v != 3.0)
+        return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1, 2 or 3");
       c->fine_block = (int)v;
       return ARP_OK;
     case ARP_OPT_TEST_SKIP_ARRIVAL:

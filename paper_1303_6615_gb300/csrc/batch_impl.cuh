@@ -48,6 +48,15 @@ __global__ void __launch_bounds__(BLOCK) fine_batch_kernel(const FineJob<T>* __r
     fine_body<T, LOGN, BLOCK>(j.in, j.out, j.steps, j.tb, blockIdx.x - first[i]);
 }
 
+// The lane-pair FP32 schedule over many problems (launch bounds as its single-problem kernel).
+template <int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, fine_pairs_min_blocks<LOGN>())
+    fine_batch_kernel_pairs(const FineJob<float>* __restrict__ jobs, const int* __restrict__ first, int njobs) {
+  const int i = find_job(first, njobs, blockIdx.x);
+  const FineJob<float> j = jobs[i];
+  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, true>(j.in, j.out, j.steps, j.tb, blockIdx.x - first[i]);
+}
+
 template <typename T, int LOGN, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) chain_batch_kernel(const ChainJob<T>* __restrict__ jobs) {
   const int i = blockIdx.x / cooperative_groups::this_cluster().num_blocks();
@@ -55,27 +64,40 @@ __global__ void __launch_bounds__(BLOCK) chain_batch_kernel(const ChainJob<T>* _
   chain_cluster_body<T, LOGN, BLOCK>(j.a, j.tb);
 }
 
-template <typename T, int LOGN, int BLOCK>
+template <typename T, int LOGN, int BLOCK, bool PAIRS = false>
 arp_status launch_fine_batch_block(arp_ctx* err, const void* jobs, const int* first, int njobs, int nblocks,
                                    cudaStream_t s) {
   constexpr bool kF32 = std::is_same<T, float>::value;
-  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK>::kBytes : FineLayout<T, LOGN>::kBytes;
-  const void* kern = (const void*)fine_batch_kernel<T, LOGN, BLOCK>;
+  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK, PAIRS>::kBytes : FineLayout<T, LOGN>::kBytes;
+  const void* kern;
+  if constexpr (PAIRS) kern = (const void*)fine_batch_kernel_pairs<LOGN, BLOCK>;
+  else kern = (const void*)fine_batch_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(err, e, "batch fine: shared-memory attribute");
+  if constexpr (PAIRS) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return check_cuda(err, e, "batch fine: shared-memory carveout");
+  }
   void* args[] = {(void*)&jobs, (void*)&first, &njobs};
   return check_cuda(err, cudaLaunchKernel(kern, dim3(nblocks), dim3(BLOCK), args, smem, s), "batch fine: launch");
 }
 
 // `tune` is a member context of the group: its ARP_OPT_FINE_BLOCK (or the
-// per-size default) sets the FP32 block size, as for one context.
+// tuned per-size default) sets the FP32 schedule, as for one context.
 template <typename T, int LOGN>
 arp_status launch_fine_batch_n(arp_ctx* err, arp_ctx* tune, const void* jobs, const int* first, int njobs,
                                int nblocks, cudaStream_t s) {
   constexpr int B0 = FineBlock<LOGN>::value, B1 = FineBlockAlt<LOGN>::value;
-  if constexpr (std::is_same<T, float>::value && B0 != B1) {
-    if (fine_choice_f32<LOGN>(tune) == 1)
-      return launch_fine_batch_block<T, LOGN, B1>(err, jobs, first, njobs, nblocks, s);
+  if constexpr (std::is_same<T, float>::value) {
+    const int v = fine_schedule_f32<LOGN>(tune);
+    if constexpr (fine_pairs_available(LOGN)) {
+      if (v == 3)
+        return launch_fine_batch_block<T, LOGN, FinePairBlock<LOGN>::value, true>(err, jobs, first, njobs, nblocks,
+                                                                                  s);
+    }
+    if constexpr (B0 != B1) {
+      if (v == 2) return launch_fine_batch_block<T, LOGN, B1>(err, jobs, first, njobs, nblocks, s);
+    }
   }
   return launch_fine_batch_block<T, LOGN, B0>(err, jobs, first, njobs, nblocks, s);
 }

@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "context.h"
+#include "fine_schedule.h"
 #include "spectral.cuh"
 
 namespace arp {
@@ -63,11 +64,7 @@ constexpr int kSchemeIfrk4 = 1;
 
 template <int LOGN> struct FineBlock {
   static constexpr int N = 1 << LOGN;
-#ifdef ARP_FINE_EIGHTH
-  static constexpr int value = LOGN >= 10 ? N / 8 : (N / 4 < 32 ? 32 : (N / 4 > 512 ? 512 : N / 4));
-#else
   static constexpr int value = N / 4 < 32 ? 32 : (N / 4 > 512 ? 512 : N / 4);
-#endif
 };
 
 // Second block size of the FP32 fine sweep: N/2 threads (at most 512).
@@ -75,6 +72,15 @@ template <int LOGN> struct FineBlockAlt {
   static constexpr int N = 1 << LOGN;
   static constexpr int value = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
 };
+
+// Third schedule of the FP32 ETDRK4 sweep (N >= 256): N/8 threads, each
+// butterfly item covering both FFT lanes at once (radix8_stage_pairs), and
+// N(u), a1 and the update sum in shared memory instead of registers, so that
+// the kernel fits in 128 registers and up to four slices share an SM.
+template <int LOGN> struct FinePairBlock {
+  static constexpr int value = (1 << LOGN) / 8;
+};
+__host__ __device__ constexpr bool fine_pairs_available(int logn) { return logn >= 8; }
 
 template <typename T>
 constexpr int fine_mode_arrays() {
@@ -277,15 +283,11 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
 // the update sum (FP32 for ETDRK4, a float pair for integrating-factor RK4) for
 // the three branches; shared memory holds only the two FFT lanes, the twiddle
 // tables and the eigenvector constants.
-template <int LOGN, int BLOCK>
+template <int LOGN, int BLOCK, bool PAIRS = false>
 struct F32Layout {
   static constexpr int K1 = ((1 << LOGN) - 1) / 3 + 1;
   static constexpr int kMPT = (K1 + BLOCK - 1) / BLOCK;
-#ifdef ARP_FINE_SMEM_STATE
-  static constexpr bool kSmemState = LOGN >= 10 && BLOCK * 8 == (1 << LOGN);
-#else
-  static constexpr bool kSmemState = false;
-#endif
+  static constexpr bool kSmemState = PAIRS;  // N(u), a1, acc in shared memory, [3][3][K1]
   static constexpr size_t kBytes = (size_t)lanes_and_twiddles<float>(LOGN) * sizeof(cf) +
                                    (size_t)2 * K1 * sizeof(float) + (kSmemState ? (size_t)9 * K1 * sizeof(cf) : 0);
 };
@@ -318,22 +320,23 @@ __device__ __forceinline__ cf etd32_stage(int stage, int i, cf bn, cf& u, cf& ul
   }
 }
 
-template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
+template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, bool PAIRS = false>
 __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
                                               const FineTabs<float>& tb, int slice) {
+  static_assert(!PAIRS || SCHEME == kSchemeEtdrk4, "the lane-pair schedule runs ETDRK4");
   using T = float;
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
   constexpr int K = (N - 1) / 3;
   constexpr int K1 = K + 1;
-  constexpr int MPT = F32Layout<LOGN, BLOCK>::kMPT;
+  constexpr int MPT = F32Layout<LOGN, BLOCK, PAIRS>::kMPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cf* Z0 = reinterpret_cast<cf*>(smem_raw);
   cf* Z1 = Z0 + padded_len<T>(N);
   cf* TW = Z1 + padded_len<T>(N);
   T* IS = reinterpret_cast<T*>(TW + twiddle_count(LOGN));
   T* SS = IS + K1;
-  constexpr bool kSmemState = F32Layout<LOGN, BLOCK>::kSmemState && SCHEME == kSchemeEtdrk4;
+  constexpr bool kSmemState = F32Layout<LOGN, BLOCK, PAIRS>::kSmemState;
   cf* NUS = reinterpret_cast<cf*>(SS + K1);  // kSmemState: N(u), a1, acc in shared memory, [3][3][K1]
 
   cf u[MPT][3], ulo[MPT][3], nu[MPT][3], a1[MPT][3], acc[MPT][3], acclo[MPT][3];
@@ -366,11 +369,10 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
     const bool last = (step == steps - 1);
 #pragma unroll 1
     for (int stage = 0; stage < 4; ++stage) {
-#ifdef ARP_FINE_PAIRS
-      nonlinear_transform_pairs<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
-#else
-      nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
-#endif
+      if constexpr (PAIRS)
+        nonlinear_transform_pairs<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
+      else
+        nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);
       const bool pack_next = !(last && stage == 3);
 #pragma unroll
       for (int r = 0; r < MPT; ++r) {
@@ -440,17 +442,22 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
   }
 }
 
-#if defined(ARP_FINE_SMEM_STATE)
-#define ARP_F32_BOUNDS __launch_bounds__(BLOCK, (BLOCK >= 256 ? 65536 / (BLOCK * 128) : (F32Layout<LOGN, BLOCK>::kSmemState ? 4 : 1)))
-#elif defined(ARP_FINE_PAIRS)
-#define ARP_F32_BOUNDS __launch_bounds__(BLOCK, (BLOCK >= 256 ? 65536 / (BLOCK * 128) : 1))
-#else
-#define ARP_F32_BOUNDS __launch_bounds__(BLOCK)
-#endif
 template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
-__global__ void ARP_F32_BOUNDS fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
+__global__ void __launch_bounds__(BLOCK) fine_sweep_kernel_f32(const cd* __restrict__ in, cd* __restrict__ out,
                                                                int steps, FineTabs<float> tb) {
   fine_f32_body<LOGN, BLOCK, SCHEME>(in, out, steps, tb, blockIdx.x);
+}
+
+// The lane-pair schedule: at most 128 registers, so that four blocks of N/8
+// threads fit an SM by registers.
+template <int LOGN>
+constexpr int fine_pairs_min_blocks() {
+  return 65536 / (FinePairBlock<LOGN>::value * 128) < 4 ? 65536 / (FinePairBlock<LOGN>::value * 128) : 4;
+}
+template <int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, fine_pairs_min_blocks<LOGN>())
+    fine_sweep_kernel_f32_pairs(const cd* __restrict__ in, cd* __restrict__ out, int steps, FineTabs<float> tb) {
+  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, true>(in, out, steps, tb, blockIdx.x);
 }
 
 template <typename T>
@@ -470,21 +477,20 @@ inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
           c->E_lo32, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64, c->h};
 }
 
-template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4>
+template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, bool PAIRS = false>
 arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int steps, cudaStream_t s) {
   constexpr bool kF32 = std::is_same<T, float>::value;
-  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK>::kBytes : FineLayout<T, LOGN>::kBytes;
+  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK, PAIRS>::kBytes : FineLayout<T, LOGN>::kBytes;
   const void* kern;
-  if constexpr (kF32) kern = (const void*)fine_sweep_kernel_f32<LOGN, BLOCK, SCHEME>;
+  if constexpr (PAIRS) kern = (const void*)fine_sweep_kernel_f32_pairs<LOGN, BLOCK>;
+  else if constexpr (kF32) kern = (const void*)fine_sweep_kernel_f32<LOGN, BLOCK, SCHEME>;
   else kern = (const void*)fine_sweep_kernel<T, LOGN, BLOCK, SCHEME>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");
-  if constexpr (kF32) {
-    if (F32Layout<LOGN, BLOCK>::kSmemState) {
-      // four such blocks per SM need the largest shared-memory carveout
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory carveout");
-    }
+  if constexpr (PAIRS) {
+    // several such blocks per SM need the largest shared-memory carveout
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory carveout");
   }
   FineTabs<T> tb = fine_tabs<T>(c);
   void* args[] = {(void*)&in, (void*)&out, &steps, &tb};
@@ -492,31 +498,34 @@ arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int s
   return check_cuda(c, e, "fine: launch");
 }
 
-// Default thread count of the FP32 fine sweep per grid size: true where the
-// FineBlockAlt variant (N/2 threads) ran faster than FineBlock (N/4) on GB300
-// (256 slices of 200 to 391 steps: faster by 32% at N=128, 6% at N=256, 9% at
-// N=512, slower by 11% at N=1024; the two coincide at N<=64 and N=2048).
-// The choice is fixed per grid size, not timed at run time: the two variants
-// round differently in the last bit (the compiler contracts and schedules the
-// differently unrolled loops differently), and results must not depend on a
-// timing decision.
-template <int LOGN> struct FineAltDefault {
-  static constexpr bool value = LOGN >= 7 && LOGN <= 9;
-};
-
-// 1 when the FP32 fine sweep at this grid size runs with FineBlockAlt threads:
-// ARP_OPT_FINE_BLOCK of context c if set, else FineAltDefault.
-template <int LOGN>
-int fine_choice_f32(const arp_ctx* c) {
-  if constexpr (FineBlock<LOGN>::value == FineBlockAlt<LOGN>::value) return 0;
-  else return c->fine_block == 1 ? 0 : (c->fine_block == 2 ? 1 : (FineAltDefault<LOGN>::value ? 1 : 0));
+// The FP32 fine sweep's schedule per grid size: 1 = N/4 threads, 2 = N/2
+// threads, 3 = the lane-pair schedule with N/8 threads (ETDRK4, N >= 256).
+// ARP_OPT_FINE_BLOCK of context c if set, else the offline-tuned table
+// (fine_schedule.h, written by the project's tuner from timings on GB300; the
+// schedules round differently in the last bits, so the choice is fixed per
+// grid size rather than timed at run time, and a result never depends on a
+// timing decision).  A schedule that does not apply falls back to the table's.
+template <int LOGN, int SCHEME = kSchemeEtdrk4>
+int fine_schedule_f32(const arp_ctx* c) {
+  const int tuned = kFineScheduleF32[LOGN];
+  int v = c->fine_block != 0 ? c->fine_block : tuned;
+  if (v == 3 && !(fine_pairs_available(LOGN) && SCHEME == kSchemeEtdrk4)) v = tuned == 3 ? 1 : tuned;
+  if (v == 2 && FineBlock<LOGN>::value == FineBlockAlt<LOGN>::value) v = 1;
+  return v;
 }
 
 template <typename T, int LOGN, int SCHEME = kSchemeEtdrk4>
 arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStream_t s) {
   constexpr int B0 = FineBlock<LOGN>::value, B1 = FineBlockAlt<LOGN>::value;
-  if constexpr (std::is_same<T, float>::value && B0 != B1) {
-    if (fine_choice_f32<LOGN>(c) == 1) return launch_fine_block<T, LOGN, B1, SCHEME>(c, in, out, batch, c->steps, s);
+  if constexpr (std::is_same<T, float>::value) {
+    const int v = fine_schedule_f32<LOGN, SCHEME>(c);
+    if constexpr (fine_pairs_available(LOGN) && SCHEME == kSchemeEtdrk4) {
+      if (v == 3)
+        return launch_fine_block<T, LOGN, FinePairBlock<LOGN>::value, SCHEME, true>(c, in, out, batch, c->steps, s);
+    }
+    if constexpr (B0 != B1) {
+      if (v == 2) return launch_fine_block<T, LOGN, B1, SCHEME>(c, in, out, batch, c->steps, s);
+    }
   }
   return launch_fine_block<T, LOGN, B0, SCHEME>(c, in, out, batch, c->steps, s);
 }
