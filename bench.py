@@ -50,7 +50,8 @@ CPU_SAMPLE_SLICES = 8           # cpu_baseline sample, one core (about 10-20 s o
 CPU_PARALLEL_SLICES_PER_CORE = 2  # cpu_baseline sample in parallel over slices: slices per host core
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fine-sweep kernel on a workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
-FINE_TRAFFIC_BYTES = {}
+FINE_TRAFFIC_BYTES = {("rsw-N1024-eps1e-4-S512-M128", "fp32"): 8725760,   # fine_sweep_kernel_f32_pairs<10,128>
+                      ("rsw-N512-eps1e-3-S256-M64", "fp32"): 2256896}     # fine_sweep_kernel_f32<9,256>
 REFERENCE_SAMPLE_SLICES = 2     # per-step sample of the reference arm
 
 
@@ -100,6 +101,8 @@ def parse():
                          "one level-by-level iteration of the headline workload (the whole-sweep fine launch and "
                          "the whole-chain cluster launch), a case for profilers")
     ap.add_argument("--instances", type=int, default=1024)
+    ap.add_argument("--kernels-workload", choices=["n1024", "n512"], default="n1024",
+                    help="with --mode kernels: the N=1024 headline workload or the N=512 instance")
     ap.add_argument("--probe", action="store_true",
                     help="with --mode dftgemm: only one small time average (a case sized for a profiler)")
     return ap.parse_args()
@@ -323,7 +326,8 @@ def run_ours(args, rank: int, world: int, w=None, timed_steps: int | None = None
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": FINE_TRAFFIC_BYTES.get((w.name, args.precision)),
-                     "kernel": "fine_sweep_kernel_f32" if prec == b.ARP_FP32 else "fine_sweep_kernel",
+                     "kernel": (("fine_sweep_kernel_f32_pairs" if w.n_grid >= 1024 else "fine_sweep_kernel_f32")
+                                if prec == b.ARP_FP32 else "fine_sweep_kernel"),
                      "launch_ms": fine_ms, "flop_per_launch": flops,
                      "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec == b.ARP_FP32
                                      else "FP64 nominal 1.25 TFLOP/s"),
@@ -1127,16 +1131,17 @@ def serve_one_rate(rate: float = 100.0, count: int = 64, seed: int = 3000) -> di
 
 
 def run_kernels(args) -> dict:
-    """The headline workload's two dominant kernels in their level-by-level
-    launches (ARP_OPT_PIPELINE 0): the predictor's chain (one cluster launch
-    over all 256 links), then one iteration: the fine sweep of all 256
-    slices in one launch, the correction, the chain, the norm."""
+    """A workload's two dominant kernels in their level-by-level launches
+    (ARP_OPT_PIPELINE 0): the predictor's chain (one cluster launch over all
+    links), then one iteration: the fine sweep of all slices in one launch, the
+    correction, the chain, the norm.  --kernels-workload picks the headline
+    workload (n1024, default) or the single large instance (n512)."""
     import torch
 
     from paper_1303_6615_gb300 import binding as b
     from paper_1303_6615_gb300 import build as bld
     bld.build()
-    w = LARGE
+    w = WORKLOAD if args.kernels_workload == "n1024" else LARGE
     prec = b.ARP_FP32 if args.precision == "fp32" else b.ARP_FP64
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:

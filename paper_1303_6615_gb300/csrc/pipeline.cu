@@ -25,6 +25,7 @@
 #include <cuda.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -254,6 +255,15 @@ arp_status make_chunks(arp_ctx* c, Pipe& p, int chunk) {
 // cluster does not fit.
 arp_status make_pipe(arp_ctx* c, Pipe& p) {
   const Driver& d = driver();
+  // A profiler attaches through an injection library; Nsight Compute fails to
+  // prepare kernels launched on green-context streams ("Failed to prepare
+  // kernel for profiling") and then ends the application, so with one attached
+  // the solve runs level by level (the same kernels per slice and per link).
+  const char* inj = std::getenv("CUDA_INJECTION64_PATH");
+  if (inj && *inj) {
+    p.why = "an injection library (a profiler) is attached; green-context launches cannot be profiled";
+    return ARP_OK;
+  }
   Partition* part = shared_partition(c->device);
   if (!part->ok) {
     p.why = part->why;
