@@ -36,6 +36,9 @@ struct arp_ctx {
   arp::cd* etd64 = nullptr;      // [6][3][K1]: E, E2, Q, f1, f2x2, f3
   arp::cf* etd32 = nullptr;
   arp::cf* E_lo32 = nullptr;     // [3][K1]: E - (double)(float)E, rounded to float
+  // compact FP32 ETDRK4 tables (E, E2, Q, f1, f2x2, f3, E_lo): [7][K1] complex of
+  // the alpha = +1 branch, then [7][K1] float of the (real) alpha = 0 branch
+  arp::cf* etd32c = nullptr;
   arp::cd* tw64 = nullptr;       // [N] (twiddle_count(logN) used): per-stage FFT twiddles
   arp::cf* tw32 = nullptr;
   arp::cd* phase64 = nullptr;    // [M][3][K1] e^{-i omega s_m}

@@ -50,6 +50,7 @@ template <typename T>
 struct FineTabs {
   EtdView<T> etd;
   const cf* E_lo;  // FP32 path: low part of E, [3][K1]
+  const cf* etdc;  // FP32 path: compact tables, [7][K1] complex (alpha = +1) then [7][K1] float (alpha = 0)
   const cpx<T>* tw;
   const T* is;
   const T* ss;
@@ -320,6 +321,65 @@ __device__ __forceinline__ cf etd32_stage(int stage, int i, cf bn, cf& u, cf& ul
   }
 }
 
+// The FP32 ETDRK4 stage of etd32_stage for all three branches of wavenumber k
+// at once, from the compact tables: the alpha = -1 coefficients are the
+// conjugates of alpha = +1's and those of alpha = 0 are real (the tables are
+// built that way), so one complex entry serves two branches and the alpha = 0
+// branch multiplies by real scalars.  N(u), a1 and the stage sum of branch q
+// are nu[q * sq], a1[q * sq], acc[q * sq].
+__device__ __forceinline__ void etd32_stage3(int stage, int k, int K1, const cf bn[3], cf u[3], cf ulo[3], cf* nu,
+                                             cf* a1, cf* acc, int sq, const cf* __restrict__ cp, cf nx[3]) {
+  const float* __restrict__ cz = reinterpret_cast<const float*>(cp + 7 * K1);
+  enum { kE = 0, kE2, kQ, kF1, kF2x2, kF3, kElo };
+  auto P = [&](int j) { return ldgc(cp + j * K1 + k); };
+  auto Z = [&](int j) { return __ldg(cz + j * K1 + k); };
+  auto rs = [](float r, cf x) { return mk<float>(r * x.x, r * x.y); };
+  if (stage == 0) {
+    const cf f1 = P(kF1), E2 = P(kE2), Q = P(kQ);
+    const float f1r = Z(kF1), E2r = Z(kE2), Qr = Z(kQ);
+#pragma unroll
+    for (int q = 0; q < 3; q += 2) {
+      const cf f = q ? f1 : conj(f1), e2 = q ? E2 : conj(E2), qq = q ? Q : conj(Q);
+      nu[q * sq] = bn[q];
+      acc[q * sq] = f * bn[q];
+      nx[q] = a1[q * sq] = e2 * u[q] + qq * bn[q];
+    }
+    nu[sq] = bn[1];
+    acc[sq] = rs(f1r, bn[1]);
+    nx[1] = a1[sq] = rs(E2r, u[1]) + rs(Qr, bn[1]);
+  } else if (stage == 3) {
+    const cf E = P(kE), El = P(kElo), f3 = P(kF3);
+    const float Er = Z(kE), Elr = Z(kElo), f3r = Z(kF3);
+#pragma unroll
+    for (int q = 0; q < 3; q += 2) {
+      const cf e = q ? E : conj(E), el = q ? El : conj(El), f = q ? f3 : conj(f3);
+      const cdf s = cdf_add(cdf_mul(e, el, u[q], ulo[q]), acc[q * sq] + f * bn[q]);
+      u[q] = mk<float>(s.re.hi, s.im.hi);
+      ulo[q] = mk<float>(s.re.lo, s.im.lo);
+      nx[q] = u[q];
+    }
+    // alpha = 0: E real, so each component is a float-pair product by the same real pair
+    const cf t = acc[sq] + rs(f3r, bn[1]);
+    const df er{Er, Elr};
+    const df re = df_add_f(df_mul_sub(er, df{u[1].x, ulo[1].x}, df{0.0f, 0.0f}, df{0.0f, 0.0f}), t.x);
+    const df im = df_add_f(df_mul_sub(er, df{u[1].y, ulo[1].y}, df{0.0f, 0.0f}, df{0.0f, 0.0f}), t.y);
+    u[1] = mk<float>(re.hi, im.hi);
+    ulo[1] = mk<float>(re.lo, im.lo);
+    nx[1] = u[1];
+  } else {
+    const cf f2 = P(kF2x2), E2 = P(kE2), Q = P(kQ);
+    const float f2r = Z(kF2x2), E2r = Z(kE2), Qr = Z(kQ);
+#pragma unroll
+    for (int q = 0; q < 3; q += 2) {
+      const cf f = q ? f2 : conj(f2), e2 = q ? E2 : conj(E2), qq = q ? Q : conj(Q);
+      acc[q * sq] = acc[q * sq] + f * bn[q];
+      nx[q] = (stage == 1) ? e2 * u[q] + qq * bn[q] : e2 * a1[q * sq] + qq * (2.0f * bn[q] - nu[q * sq]);
+    }
+    acc[sq] = acc[sq] + rs(f2r, bn[1]);
+    nx[1] = (stage == 1) ? rs(E2r, u[1]) + rs(Qr, bn[1]) : rs(E2r, a1[sq]) + rs(Qr, 2.0f * bn[1] - nu[sq]);
+  }
+}
+
 template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, bool PAIRS = false>
 __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
                                               const FineTabs<float>& tb, int slice) {
@@ -381,8 +441,14 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
         const T is = IS[k], ss = SS[k];
         cf bn[3], nx[3];
         unpack_mode<T, N>(Z0, Z1, k, is, ss, bn);
+        if constexpr (SCHEME == kSchemeEtdrk4) {
+          if constexpr (kSmemState)
+            etd32_stage3(stage, k, K1, bn, u[r], ulo[r], NUS + k, NUS + 3 * K1 + k, NUS + 6 * K1 + k, K1, tb.etdc, nx);
+          else
+            etd32_stage3(stage, k, K1, bn, u[r], ulo[r], nu[r], a1[r], acc[r], 1, tb.etdc, nx);
+        }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < 3 && SCHEME == kSchemeIfrk4; ++q) {
           const int i = q * K1 + k;
           if constexpr (SCHEME == kSchemeIfrk4) {
             const float h = (float)tb.h;
@@ -409,11 +475,6 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
               acclo[r][q] = mk<float>(re.lo, im.lo);
               nx[q] = (stage == 1) ? E2 * u[r][q] + (0.5f * h) * bn[q] : ldgc(e.E + i) * u[r][q] + h * w;
             }
-          } else if constexpr (kSmemState) {
-            nx[q] = etd32_stage(stage, i, bn[q], u[r][q], ulo[r][q], NUS[i], NUS[3 * K1 + i], NUS[6 * K1 + i], e,
-                                tb.E_lo);
-          } else {
-            nx[q] = etd32_stage(stage, i, bn[q], u[r][q], ulo[r][q], nu[r][q], a1[r][q], acc[r][q], e, tb.E_lo);
           }
         }
         if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
@@ -467,14 +528,14 @@ template <>
 inline FineTabs<double> fine_tabs<double>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd64, c->etd64 + n, c->etd64 + 2 * n, c->etd64 + 3 * n, c->etd64 + 4 * n, c->etd64 + 5 * n},
-          nullptr, c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64, c->h};
+          nullptr, nullptr, c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64, c->h};
 }
 
 template <>
 inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd32, c->etd32 + n, c->etd32 + 2 * n, c->etd32 + 3 * n, c->etd32 + 4 * n, c->etd32 + 5 * n},
-          c->E_lo32, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64, c->h};
+          c->E_lo32, c->etd32c, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64, c->h};
 }
 
 template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, bool PAIRS = false>

@@ -100,7 +100,7 @@ __device__ __forceinline__ double omega_of(int b, int k, double s) {
 // the conjugate of alpha = +1 (lambda_- = conj(lambda_+)), kept exact so that
 // real k = 0 fields stay real.
 __global__ void etd_kernel(int K1, double s, double inv_eps, double nu, double h, cd* etd64, cf* etd32,
-                           cf* elo32) {
+                           cf* elo32, cf* etd32c) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K1) return;
   const double k4 = (double)k * (double)k * (double)k * (double)k;
@@ -134,6 +134,16 @@ __global__ void etd_kernel(int K1, double s, double inv_eps, double nu, double h
     const cf el = {(float)(v[0].x - (double)eh.x), (float)(v[0].y - (double)eh.y)};
     elo32[b * K1 + k] = el;
     if (b == 2) elo32[k] = {el.x, -el.y};
+    // compact copy: alpha = +1 complex, alpha = 0 real (its imaginary parts are zero)
+    if (etd32c) {
+      const cf c7[7] = {etd32[(0 * 3 + b) * K1 + k], etd32[(1 * 3 + b) * K1 + k], etd32[(2 * 3 + b) * K1 + k],
+                        etd32[(3 * 3 + b) * K1 + k], etd32[(4 * 3 + b) * K1 + k], etd32[(5 * 3 + b) * K1 + k], el};
+      float* z = reinterpret_cast<float*>(etd32c + 7 * K1);
+      for (int j = 0; j < 7; ++j) {
+        if (b == 2) etd32c[j * K1 + k] = c7[j];
+        else z[j * K1 + k] = c7[j].x;
+      }
+    }
   }
 }
 
@@ -214,7 +224,8 @@ arp_status build_tables(arp_ctx* c, cudaStream_t st) {
   eigen_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->inv_sig64, c->sk_sig64, c->inv_sig32,
                                                            c->sk_sig32);
   twiddle_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw64, c->tw32);
-  etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32);
+  etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32,
+                                                   c->etd32c);
   weights_kernel<<<1, 256, 0, st>>>(c->M, c->weight64, c->weight32);
   phase_kernel<<<dim3((c->K1 + tb - 1) / tb, c->M < 65535 ? c->M : 65535), tb, 0, st>>>(c->M, c->K1, s, T0, c->phase64, c->phase32);
   coarse_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->nu, c->dT, inv_eps, c->dhalf, c->gphase,
