@@ -50,8 +50,8 @@ CPU_SAMPLE_SLICES = 8           # cpu_baseline sample, one core (about 10-20 s o
 CPU_PARALLEL_SLICES_PER_CORE = 2  # cpu_baseline sample in parallel over slices: slices per host core
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fine-sweep kernel on a workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
-FINE_TRAFFIC_BYTES = {("rsw-N1024-eps1e-4-S512-M128", "fp32"): 8725760,   # fine_sweep_kernel_f32_pairs<10,128>
-                      ("rsw-N512-eps1e-3-S256-M64", "fp32"): 2256896}     # fine_sweep_kernel_f32<9,256>
+FINE_TRAFFIC_BYTES = {("rsw-N1024-eps1e-4-S512-M128", "fp32", 3): 8725760,   # fine_sweep_kernel_f32_pairs<10,128>
+                      ("rsw-N512-eps1e-3-S256-M64", "fp32", 2): 2256896}     # fine_sweep_kernel_f32<9,256>
 REFERENCE_SAMPLE_SLICES = 2     # per-step sample of the reference arm
 
 
@@ -284,6 +284,7 @@ def run_ours(args, rank: int, world: int, w=None, timed_steps: int | None = None
     achieved = flops / (fine_ms / 1e3) / 1e12
     peak = FP32_ALU_PEAK_TFLOPS if prec == b.ARP_FP32 else FP64_ALU_PEAK_TFLOPS
     peak_measured = b.arp_alu_peak(prec)  # FMA chains on every SM, this GPU
+    sched = b.arp_info(ctx)["fine_schedule"]
 
     # end to end through the public API with host buffers: one complete solve per step
     # (u0 from pinned host memory, predictor + KMAX iterations, all slices back to pinned host)
@@ -325,9 +326,10 @@ def run_ours(args, rank: int, world: int, w=None, timed_steps: int | None = None
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": FINE_TRAFFIC_BYTES.get((w.name, args.precision)),
-                     "kernel": (("fine_sweep_kernel_f32_pairs" if w.n_grid >= 1024 else "fine_sweep_kernel_f32")
+                     "frac": achieved / peak, "traffic": FINE_TRAFFIC_BYTES.get((w.name, args.precision, sched)),
+                     "kernel": (("fine_sweep_kernel_f32_pairs" if sched == 3 else "fine_sweep_kernel_f32")
                                 if prec == b.ARP_FP32 else "fine_sweep_kernel"),
+                     "fine_schedule": sched,
                      "launch_ms": fine_ms, "flop_per_launch": flops,
                      "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec == b.ARP_FP32
                                      else "FP64 nominal 1.25 TFLOP/s"),
@@ -890,7 +892,7 @@ def run_precision(args) -> dict:
     fields = ("v1", "v2", "h")
     iterates = {}
     for name, prec in (("fp64", b.ARP_FP64), ("fp32", b.ARP_FP32), ("tf32x3", b.ARP_TF32X3),
-                       ("bf16x2", b.ARP_BF16X2)):
+                       ("bf16x2", b.ARP_BF16X2), ("bf16x3", b.ARP_BF16X3)):
         with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
             xin = torch.from_numpy(x).cuda()
             y = torch.empty_like(xin)
@@ -902,7 +904,7 @@ def run_precision(args) -> dict:
                    for i, f in enumerate(fields)}
             drift = float(np.max(np.abs(got[:, 2, 0] - x[:, 2, 0].real) / np.abs(x[:, 2, 0].real)))
             out["fine_sweep_vs_fp64"][name] = {"rel_l2": rel, "mean_height_drift": drift}
-            if prec in (b.ARP_TF32X3, b.ARP_BF16X2):
+            if prec in (b.ARP_TF32X3, b.ARP_BF16X2, b.ARP_BF16X3):
                 continue  # the full-size parareal comparison below is FP32 against FP64
             b.arp_set_initial(s.ctx, torch.from_numpy(w.initial_state()).cuda())
             U = torch.empty((w.slices + 1, 3, H), dtype=torch.complex128, device="cuda")

@@ -304,8 +304,9 @@ const char* arp_batch_last_error(const arp_batch* batch);
 
 /* arp_info: sizes of a context: out[0]=N, out[1]=H, out[2]=K, out[3]=slices,
  * out[4]=M, out[5]=fine steps per slice, out[6]=current level k (-1 before the
- * predictor), out[7]=precision. */
-arp_status arp_info(const arp_ctx* ctx, int* out8);
+ * predictor), out[7]=precision, out[8]=the schedule the FP32 ETDRK4 fine sweep
+ * runs with (1, 2 or 3 as ARP_OPT_FINE_BLOCK; the tuned default resolved). */
+arp_status arp_info(const arp_ctx* ctx, int* out9);
 
 /* arp_alu_peak: the measured plain-ALU peak of the current device: fused
  * multiply-adds of `precision` (ARP_FP32 or ARP_FP64) in independent register

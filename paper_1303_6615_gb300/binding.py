@@ -128,9 +128,9 @@ def arp_query_bytes(N: int, slices: int, M: int, precision: int) -> int:
 
 
 def arp_info(ctx: int) -> dict:
-    out = (ctypes.c_int * 8)()
+    out = (ctypes.c_int * 9)()
     _check(ctx, load_library().arp_info(ctx, out))
-    keys = ("N", "H", "K", "slices", "M", "steps", "level", "precision")
+    keys = ("N", "H", "K", "slices", "M", "steps", "level", "precision", "fine_schedule")
     return dict(zip(keys, list(out)))
 
 

@@ -225,6 +225,8 @@ arp_status arp_create(arp_ctx** out, int N, double eps, double nu, int slices, d
   c->steps = ratio < 1.0 ? 1 : (int)ratio;
   c->h = dT / c->steps;
   arp_status r = check_cuda(c, cudaGetDevice(&c->device), "current device");
+  if (r == ARP_OK)
+    r = check_cuda(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device), "SM count");
   if (r == ARP_OK) r = allocate(c);
   if (r == ARP_OK) {
     cudaStream_t s;
@@ -440,7 +442,7 @@ const char* arp_last_error(const arp_ctx* c) {
   return c->err.c_str();
 }
 
-arp_status arp_info(const arp_ctx* c, int* o) {
+arp_status arp_info(const arp_ctx* c, int* o) {  // o: 9 values
   if (!c || !o) return ARP_EINVAL;
   o[0] = c->N;
   o[1] = c->H;
@@ -450,6 +452,7 @@ arp_status arp_info(const arp_ctx* c, int* o) {
   o[5] = c->steps;
   o[6] = c->level;
   o[7] = c->precision;
+  o[8] = fine_schedule_in_effect(c);
   return ARP_OK;
 }
 

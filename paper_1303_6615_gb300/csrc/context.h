@@ -26,6 +26,7 @@ struct arp_ctx {
   int kmax = 5;
   int precision = ARP_FP64;
   int device = 0;
+  int num_sms = 0;               // SMs of the device (the fine sweep's schedule rule)
   bool tables_dirty = true;
 
   // FP64 tables (always), FP32 copies (rounded from FP64)
@@ -165,6 +166,8 @@ arp_status pipeline_info(const arp_ctx* c, int* out);
 // e.g. by a profiler that does not support them, rather than a fault); the
 // pipeline is then disabled for c and the caller solves level by level.
 bool pipeline_recover(arp_ctx* c);
+// fine32.cu: the FP32 ETDRK4 fine sweep's schedule in effect for c (1, 2 or 3).
+int fine_schedule_in_effect(const arp_ctx* c);
 void pipeline_release(arp_ctx* c);
 // dftgemm.cu: the DFT-as-GEMM precisions (ARP_TF32X3, ARP_BF16X2): the time
 // average's node terms as one chunk partial [batch][1][3][K1], and the ETDRK4

@@ -559,16 +559,21 @@ arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int s
   return check_cuda(c, e, "fine: launch");
 }
 
-// The FP32 fine sweep's schedule per grid size: 1 = N/4 threads, 2 = N/2
-// threads, 3 = the lane-pair schedule with N/8 threads (ETDRK4, N >= 256).
-// ARP_OPT_FINE_BLOCK of context c if set, else the offline-tuned table
-// (fine_schedule.h, written by the project's tuner from timings on GB300; the
-// schedules round differently in the last bits, so the choice is fixed per
-// grid size rather than timed at run time, and a result never depends on a
-// timing decision).  A schedule that does not apply falls back to the table's.
+// The FP32 fine sweep's schedule: 1 = N/4 threads, 2 = N/2 threads, 3 = the
+// lane-pair schedule with N/8 threads (ETDRK4, N >= 256).  ARP_OPT_FINE_BLOCK
+// of context c if set, else the offline-tuned tables (fine_schedule.h, written
+// by the project's tuner from timings on GB300): the throughput table when the
+// context's slices fill the device (at least two per SM, so every level's fine
+// work keeps the SMs busy), else the latency table (few slices per SM: the
+// sweep of one slice bounds a level).  The schedules round differently in the
+// last bits, so the choice is fixed per grid size and context shape rather
+// than timed at run time, and a result never depends on a timing decision; a
+// context keeps its schedule for every launch.  A schedule that does not
+// apply falls back to the table's.
 template <int LOGN, int SCHEME = kSchemeEtdrk4>
 int fine_schedule_f32(const arp_ctx* c) {
-  const int tuned = kFineScheduleF32[LOGN];
+  const bool fills = c->num_sms > 0 && c->slices >= 2 * c->num_sms;
+  const int tuned = fills ? kFineScheduleF32Tp[LOGN] : kFineScheduleF32Lat[LOGN];
   int v = c->fine_block != 0 ? c->fine_block : tuned;
   if (v == 3 && !(fine_pairs_available(LOGN) && SCHEME == kSchemeEtdrk4)) v = tuned == 3 ? 1 : tuned;
   if (v == 2 && FineBlock<LOGN>::value == FineBlockAlt<LOGN>::value) v = 1;

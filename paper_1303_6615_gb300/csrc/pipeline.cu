@@ -174,10 +174,7 @@ void make_partition(Partition& part, int device) {
     return;
   }
   unsigned nb = 1;
-#ifndef ARP_CHAIN_SMS
-#define ARP_CHAIN_SMS 16
-#endif
-  if (d.split(&grp, &nb, &all, &rest, CU_DEV_SM_RESOURCE_SPLIT_MAX_POTENTIAL_CLUSTER_SIZE, ARP_CHAIN_SMS) != CUDA_SUCCESS ||
+  if (d.split(&grp, &nb, &all, &rest, CU_DEV_SM_RESOURCE_SPLIT_MAX_POTENTIAL_CLUSTER_SIZE, 16) != CUDA_SUCCESS ||
       nb < 1 || rest.sm.smCount < 1) {
     part.why = "the SMs cannot be split into a chain group and a fine group";
     return;

@@ -75,7 +75,8 @@ def test_info_and_host_initial_state():
     w, p, u0 = _small()
     with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad) as s:
         info = b.arp_info(s.ctx)
-        assert info == {"N": 64, "H": 33, "K": 21, "slices": 16, "M": 32, "steps": 63, "level": -1, "precision": 0}
+        assert info == {"N": 64, "H": 33, "K": 21, "slices": 16, "M": 32, "steps": 63, "level": -1, "precision": 0,
+                        "fine_schedule": 1}
         b.arp_set_initial(s.ctx, torch.from_numpy(u0))  # pageable host memory
         b.arp_parareal_iterate(s.ctx)
         U = torch.empty((w.slices + 1, 3, 33), dtype=torch.complex128)
