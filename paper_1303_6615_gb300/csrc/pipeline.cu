@@ -255,14 +255,18 @@ arp_status make_chunks(arp_ctx* c, Pipe& p, int chunk) {
 // cluster does not fit.
 arp_status make_pipe(arp_ctx* c, Pipe& p) {
   const Driver& d = driver();
-  // A profiler attaches through an injection library; Nsight Compute fails to
-  // prepare kernels launched on green-context streams ("Failed to prepare
-  // kernel for profiling") and then ends the application, so with one attached
-  // the solve runs level by level (the same kernels per slice and per link).
-  const char* inj = std::getenv("CUDA_INJECTION64_PATH");
-  if (inj && *inj) {
-    p.why = "an injection library (a profiler) is attached; green-context launches cannot be profiled";
-    return ARP_OK;
+  // A profiler attaches through an injection library (announced in the
+  // environment); Nsight Compute fails to prepare the chain's cluster kernel
+  // launched on a green-context stream ("Failed to prepare kernel for
+  // profiling") and then ends the application, so with one attached the solve
+  // runs level by level (the same kernels per slice and per link).
+  for (const char* var : {"CUDA_INJECTION64_PATH", "NV_NSIGHT_INJECTION_TRANSPORT_TYPE",
+                          "NV_COMPUTE_PROFILER_PERFWORKS_DIR"}) {
+    const char* v = std::getenv(var);
+    if (v && *v) {
+      p.why = "a profiler is attached; green-context launches cannot be profiled";
+      return ARP_OK;
+    }
   }
   Partition* part = shared_partition(c->device);
   if (!part->ok) {
