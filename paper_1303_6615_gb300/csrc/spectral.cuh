@@ -94,6 +94,31 @@ __host__ __device__ constexpr int padded_len(int n) {
   return swizzled_lanes<T>(n) ? n : n + (n >> Pad<T>::kShift);
 }
 
+// S(bits 4-6 of i): the swizzle term of pidx for swizzled lanes.
+__host__ __device__ __forceinline__ constexpr int swz_term(int i) {
+  return (int)((0xCFA95630u >> (((unsigned)i >> 2) & 28u)) & 15u);
+}
+
+// Positions pidx(base + q e), q = 0..7, of one radix-8 butterfly whose base
+// and offsets occupy disjoint bits (base = g 8e + j with j < e, e a power of
+// two): bits 4-6 of base + q e are then those of base XOR those of q e, and S
+// is linear over GF(2), so the swizzle splits into S(base), computed once,
+// and S(q e), a constant once e is known at compile time; for e >= 16 the
+// offsets q e leave bits 0-3 alone and stay plain additions.  Equal to pidx
+// term by term.
+template <typename T, int N>
+__device__ __forceinline__ void butterfly_positions(int base, int e, int at[8]) {
+  if constexpr (swizzled_lanes<T>(N)) {
+    const int sb = base ^ swz_term(base);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      at[q] = e >= 16 ? (sb ^ swz_term(q * e)) + q * e : (base + q * e) ^ swz_term(base) ^ swz_term(q * e);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) at[q] = pidx<T, N>(base + q * e);
+  }
+}
+
 // Last wavenumber whose bins k and N-k must be zero before an inverse
 // transform.  The first outer inverse stage (span N) reads bin j + q N/8 as its
 // q-th input; the 2/3 rule leaves bins 3N/8 .. 5N/8-1 (q = 3, 4) zero, so that
@@ -249,11 +274,13 @@ __device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>
     cpx<T>* Zl = Z + lane * PL;
     const int j = bidx & (e - 1);
     const int base = ((bidx >> (logL - 3)) << logL) + j;
+    int at[8];
+    butterfly_positions<T, N>(base, e, at);
     cpx<T> x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       if (PRUNE == 1 && (q == 3 || q == 4)) continue;
-      x[q] = Zl[pidx<T, N>(base + q * e)];
+      x[q] = Zl[at[q]];
     }
     if (!DIF && j) {
 #pragma unroll
@@ -270,7 +297,7 @@ __device__ __forceinline__ void radix8_stage(cpx<T>* Z, int nlanes, const cpx<T>
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       if (PRUNE == 2 && (q == 3 || q == 4)) continue;
-      Zl[pidx<T, N>(base + q * e)] = x[q];
+      Zl[at[q]] = x[q];
     }
   }
 }
@@ -295,8 +322,7 @@ __device__ __forceinline__ void radix8_stage_pairs(cpx<T>* Z, int npairs, const 
     const int j = bidx & (e - 1);
     const int base = ((bidx >> (logL - 3)) << logL) + j;
     int at[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) at[q] = pidx<T, N>(base + q * e);
+    butterfly_positions<T, N>(base, e, at);
     cpx<T> x[8], y[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -359,11 +385,17 @@ __device__ __forceinline__ void middle_stage(cpx<T>* Z, int npairs) {
     const int i = item - pair * (N / R);
     cpx<T>* Z0 = Z + 2 * pair * PL;
     cpx<T>* Z1 = Z0 + PL;
+    // positions pidx(R i + q): R i and q < R <= 8 occupy disjoint bits below bit 4
+    // for q, so the swizzle term is that of R i (XORing q in is adding it)
+    int at[8];
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      at[q] = swizzled_lanes<T>(N) ? ((R * i) ^ swz_term(R * i)) ^ q : pidx<T, N>(R * i + q);
     cpx<T> a[8], b[8];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      a[q] = Z0[pidx<T, N>(R * i + q)];
-      b[q] = Z1[pidx<T, N>(R * i + q)];
+      a[q] = Z0[at[q]];
+      b[q] = Z1[at[q]];
     }
     if (R == 8) {
       dft8<T, +1>(a);
@@ -389,8 +421,8 @@ __device__ __forceinline__ void middle_stage(cpx<T>* Z, int npairs) {
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      Z0[pidx<T, N>(R * i + q)] = a[q];
-      Z1[pidx<T, N>(R * i + q)] = b[q];
+      Z0[at[q]] = a[q];
+      Z1[at[q]] = b[q];
     }
   }
 }
