@@ -51,6 +51,7 @@ CPU_PARALLEL_SLICES_PER_CORE = 2  # cpu_baseline sample in parallel over slices:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fine-sweep kernel on a workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
 FINE_TRAFFIC_BYTES = {("rsw-N1024-eps1e-4-S512-M128", "fp32", 3): 8725760,   # fine_sweep_kernel_f32_pairs<10,128>
+                      ("rsw-N1024-eps1e-4-S512-M128", "fp32", 4): None,      # fine_sweep_kernel_f32_r16<10,128>
                       ("rsw-N512-eps1e-3-S256-M64", "fp32", 2): 2256896}     # fine_sweep_kernel_f32<9,256>
 REFERENCE_SAMPLE_SLICES = 2     # per-step sample of the reference arm
 
@@ -327,8 +328,8 @@ def run_ours(args, rank: int, world: int, w=None, timed_steps: int | None = None
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": FINE_TRAFFIC_BYTES.get((w.name, args.precision, sched)),
-                     "kernel": (("fine_sweep_kernel_f32_pairs" if sched == 3 else "fine_sweep_kernel_f32")
-                                if prec == b.ARP_FP32 else "fine_sweep_kernel"),
+                     "kernel": ({3: "fine_sweep_kernel_f32_pairs", 4: "fine_sweep_kernel_f32_r16"}.get(
+                                    sched, "fine_sweep_kernel_f32") if prec == b.ARP_FP32 else "fine_sweep_kernel"),
                      "fine_schedule": sched,
                      "launch_ms": fine_ms, "flop_per_launch": flops,
                      "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 x 2.07 GHz" if prec == b.ARP_FP32

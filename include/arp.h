@@ -89,7 +89,9 @@ typedef enum {
                               (chosen offline from GB300 timings), 1 = N/4 threads per slice,
                               2 = N/2 threads (both at least 32, at most 512), 3 = N/8 threads
                               with both FFT lanes per butterfly and the ETDRK4 stage values in
-                              shared memory (ETDRK4, N >= 256; elsewhere the default applies);
+                              shared memory (ETDRK4, N >= 256), 4 = N/8 threads with radix-16
+                              transform stages and the stage values in shared memory (ETDRK4,
+                              512 <= N <= 2048); where 3 or 4 does not apply the default does;
                               all are within the FP32 error bound, their results differ in the
                               last bits (default 0) */
   ARP_OPT_FINE_SCHEME = 8,  /* fine propagator F: 0 = ETDRK4 (Cox & Matthews, default), 1 = Strang
@@ -305,7 +307,7 @@ const char* arp_batch_last_error(const arp_batch* batch);
 /* arp_info: sizes of a context: out[0]=N, out[1]=H, out[2]=K, out[3]=slices,
  * out[4]=M, out[5]=fine steps per slice, out[6]=current level k (-1 before the
  * predictor), out[7]=precision, out[8]=the schedule the FP32 ETDRK4 fine sweep
- * runs with (1, 2 or 3 as ARP_OPT_FINE_BLOCK; the tuned default resolved). */
+ * runs with (1 to 4 as ARP_OPT_FINE_BLOCK; the tuned default resolved). */
 arp_status arp_info(const arp_ctx* ctx, int* out9);
 
 /* arp_alu_peak: the measured plain-ALU peak of the current device: fused

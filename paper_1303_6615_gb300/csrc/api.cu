@@ -80,7 +80,7 @@ Sizes sizes_of(int N, int slices, int M) {
   const size_t P = (M + qc - 1) / qc;
   const size_t CC = coarse_chunk(slices, P, K1);
   Sizes z;
-  z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (size_t)N * (16 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
+  z.tables = K1 * (8 + 8 + 4 + 4) + 18 * K1 * (16 + 8) + 3 * K1 * 8 + (size_t)N * (16 + 8 + 8) + (size_t)M * 3 * K1 * (16 + 8) +
              (size_t)M * 12 + K1 * 8 + 3 * K1 * 16 + 3 * K1 * 16 + 7 * K1 * 12;
   z.work = 2 * CC * 3 * K1 * 16 + (CC + 1) * P * 3 * K1 * 16 + (S + 1) * 8 + 16 + 16;
   z.state = 2 * (S + 1) * 3 * H * 16 + 3 * S * 3 * H * 16 + 2 * S * 3 * K1 * 16;
@@ -107,7 +107,7 @@ void release(arp_ctx* c) {
                   c->tw32,      c->phase64,  c->phase32,   c->weight64,  c->weight32, c->dhalf, c->gphase,
                   c->W,         c->W2,       c->partial,   c->rel,       c->scalar,   c->U,     c->Uold,
                   c->Gc,        c->Fb,       c->V,         c->sync,     c->part2,    c->VT,    c->Ge,
-                  c->strang_h64, c->etd32c};
+                  c->strang_h64, c->etd32c,  c->tw16_32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -127,6 +127,7 @@ arp_status allocate(arp_ctx* c) {
   ARP_ALLOC(c->etd32c, 7 * K1 * 8 + 7 * K1 * 4);
   ARP_ALLOC(c->tw64, N * 16);
   ARP_ALLOC(c->tw32, N * 8);
+  ARP_ALLOC(c->tw16_32, N * 8);
   ARP_ALLOC(c->phase64, M * 3 * K1 * 16);
   ARP_ALLOC(c->phase32, M * 3 * K1 * 8);
   ARP_ALLOC(c->weight64, M * 8);
@@ -305,8 +306,8 @@ arp_status arp_set_option(arp_ctx* c, int key, double v) {
       c->pipeline = (int)v;
       return ARP_OK;
     case ARP_OPT_FINE_BLOCK:
-      if (v != 0.0 && v != 1.0 && v != 2.0 && v != 3.0)
-        return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1, 2 or 3");
+      if (v != 0.0 && v != 1.0 && v != 2.0 && v != 3.0 && v != 4.0)
+        return fail(c, ARP_EINVAL, "FINE_BLOCK must be 0, 1, 2, 3 or 4");
       c->fine_block = (int)v;
       return ARP_OK;
     case ARP_OPT_TEST_SKIP_ARRIVAL:

@@ -54,7 +54,16 @@ __global__ void __launch_bounds__(BLOCK, fine_pairs_min_blocks<LOGN>())
     fine_batch_kernel_pairs(const FineJob<float>* __restrict__ jobs, const int* __restrict__ first, int njobs) {
   const int i = find_job(first, njobs, blockIdx.x);
   const FineJob<float> j = jobs[i];
-  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, true>(j.in, j.out, j.steps, j.tb, blockIdx.x - first[i]);
+  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, kPlanPairs>(j.in, j.out, j.steps, j.tb, blockIdx.x - first[i]);
+}
+
+// The radix-16 FP32 schedule over many problems.
+template <int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, fine_pairs_min_blocks<LOGN>())
+    fine_batch_kernel_r16(const FineJob<float>* __restrict__ jobs, const int* __restrict__ first, int njobs) {
+  const int i = find_job(first, njobs, blockIdx.x);
+  const FineJob<float> j = jobs[i];
+  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, kPlanRadix16>(j.in, j.out, j.steps, j.tb, blockIdx.x - first[i]);
 }
 
 template <typename T, int LOGN, int BLOCK>
@@ -64,17 +73,18 @@ __global__ void __launch_bounds__(BLOCK) chain_batch_kernel(const ChainJob<T>* _
   chain_cluster_body<T, LOGN, BLOCK>(j.a, j.tb);
 }
 
-template <typename T, int LOGN, int BLOCK, bool PAIRS = false>
+template <typename T, int LOGN, int BLOCK, int PLAN = kPlanRadix8>
 arp_status launch_fine_batch_block(arp_ctx* err, const void* jobs, const int* first, int njobs, int nblocks,
                                    cudaStream_t s) {
   constexpr bool kF32 = std::is_same<T, float>::value;
-  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK, PAIRS>::kBytes : FineLayout<T, LOGN>::kBytes;
+  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK, PLAN>::kBytes : FineLayout<T, LOGN>::kBytes;
   const void* kern;
-  if constexpr (PAIRS) kern = (const void*)fine_batch_kernel_pairs<LOGN, BLOCK>;
+  if constexpr (PLAN == kPlanRadix16) kern = (const void*)fine_batch_kernel_r16<LOGN, BLOCK>;
+  else if constexpr (PLAN == kPlanPairs) kern = (const void*)fine_batch_kernel_pairs<LOGN, BLOCK>;
   else kern = (const void*)fine_batch_kernel<T, LOGN, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(err, e, "batch fine: shared-memory attribute");
-  if constexpr (PAIRS) {
+  if constexpr (PLAN != kPlanRadix8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return check_cuda(err, e, "batch fine: shared-memory carveout");
   }
@@ -90,10 +100,15 @@ arp_status launch_fine_batch_n(arp_ctx* err, arp_ctx* tune, const void* jobs, co
   constexpr int B0 = FineBlock<LOGN>::value, B1 = FineBlockAlt<LOGN>::value;
   if constexpr (std::is_same<T, float>::value) {
     const int v = fine_schedule_f32<LOGN>(tune);
+    if constexpr (r16_available(LOGN)) {
+      if (v == 4)
+        return launch_fine_batch_block<T, LOGN, FinePairBlock<LOGN>::value, kPlanRadix16>(err, jobs, first, njobs,
+                                                                                         nblocks, s);
+    }
     if constexpr (fine_pairs_available(LOGN)) {
       if (v == 3)
-        return launch_fine_batch_block<T, LOGN, FinePairBlock<LOGN>::value, true>(err, jobs, first, njobs, nblocks,
-                                                                                  s);
+        return launch_fine_batch_block<T, LOGN, FinePairBlock<LOGN>::value, kPlanPairs>(err, jobs, first, njobs,
+                                                                                       nblocks, s);
     }
     if constexpr (B0 != B1) {
       if (v == 2) return launch_fine_batch_block<T, LOGN, B1>(err, jobs, first, njobs, nblocks, s);

@@ -42,6 +42,7 @@ struct arp_ctx {
   arp::cf* etd32c = nullptr;
   arp::cd* tw64 = nullptr;       // [N] (twiddle_count(logN) used): per-stage FFT twiddles
   arp::cf* tw32 = nullptr;
+  arp::cf* tw16_32 = nullptr;    // [N] (twiddle16_count(logN) used, 512 <= N <= 2048): radix-16 twiddles
   arp::cd* phase64 = nullptr;    // [M][3][K1] e^{-i omega s_m}
   arp::cf* phase32 = nullptr;
   double* weight64 = nullptr;    // [M] w_m

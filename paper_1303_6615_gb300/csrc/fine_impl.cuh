@@ -33,6 +33,7 @@
 #include "context.h"
 #include "fine_schedule.h"
 #include "spectral.cuh"
+#include "spectral16.cuh"
 
 namespace arp {
 
@@ -52,6 +53,7 @@ struct FineTabs {
   const cf* E_lo;  // FP32 path: low part of E, [3][K1]
   const cf* etdc;  // FP32 path: compact tables, [7][K1] complex (alpha = +1) then [7][K1] float (alpha = 0)
   const cpx<T>* tw;
+  const cf* tw16;  // FP32 path, 512 <= N <= 2048: the radix-16 plan's twiddles
   const T* is;
   const T* ss;
   const double* is64;
@@ -82,6 +84,15 @@ template <int LOGN> struct FinePairBlock {
   static constexpr int value = (1 << LOGN) / 8;
 };
 __host__ __device__ constexpr bool fine_pairs_available(int logn) { return logn >= 8; }
+
+// Transform plans of the FP32 sweep: radix-8 stages on one lane per item (the
+// N/4 and N/2 schedules, state in registers); radix-8 stages on both lanes per
+// item (the lane-pair schedule); radix-16 outer stages on one lane per item
+// (spectral16.cuh, 512 <= N <= 2048, N/8 threads).  The last two keep N(u),
+// a1 and the update sum in shared memory.
+constexpr int kPlanRadix8 = 0;
+constexpr int kPlanPairs = 1;
+constexpr int kPlanRadix16 = 2;
 
 template <typename T>
 constexpr int fine_mode_arrays() {
@@ -284,12 +295,13 @@ __global__ void __launch_bounds__(BLOCK) fine_sweep_kernel(const cd* __restrict_
 // the update sum (FP32 for ETDRK4, a float pair for integrating-factor RK4) for
 // the three branches; shared memory holds only the two FFT lanes, the twiddle
 // tables and the eigenvector constants.
-template <int LOGN, int BLOCK, bool PAIRS = false>
+template <int LOGN, int BLOCK, int PLAN = kPlanRadix8>
 struct F32Layout {
   static constexpr int K1 = ((1 << LOGN) - 1) / 3 + 1;
   static constexpr int kMPT = (K1 + BLOCK - 1) / BLOCK;
-  static constexpr bool kSmemState = PAIRS;  // N(u), a1, acc in shared memory, [3][3][K1]
-  static constexpr size_t kBytes = (size_t)lanes_and_twiddles<float>(LOGN) * sizeof(cf) +
+  static constexpr bool kSmemState = PLAN != kPlanRadix8;  // N(u), a1, acc in shared memory, [3][3][K1]
+  static constexpr int kTwiddles = PLAN == kPlanRadix16 ? twiddle16_count(LOGN) : twiddle_count(LOGN);
+  static constexpr size_t kBytes = (size_t)(2 * padded_len<float>(1 << LOGN) + kTwiddles) * sizeof(cf) +
                                    (size_t)2 * K1 * sizeof(float) + (kSmemState ? (size_t)9 * K1 * sizeof(cf) : 0);
 };
 
@@ -380,28 +392,32 @@ __device__ __forceinline__ void etd32_stage3(int stage, int k, int K1, const cf 
   }
 }
 
-template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, bool PAIRS = false>
+template <int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, int PLAN = kPlanRadix8>
 __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __restrict__ out, int steps,
                                               const FineTabs<float>& tb, int slice) {
-  static_assert(!PAIRS || SCHEME == kSchemeEtdrk4, "the lane-pair schedule runs ETDRK4");
+  static_assert(PLAN == kPlanRadix8 || SCHEME == kSchemeEtdrk4, "the shared-state schedules run ETDRK4");
+  static_assert(PLAN != kPlanRadix16 || r16_available(LOGN), "the radix-16 plan covers 512 <= N <= 2048");
   using T = float;
   constexpr int N = 1 << LOGN;
   constexpr int H = N / 2 + 1;
   constexpr int K = (N - 1) / 3;
   constexpr int K1 = K + 1;
-  constexpr int MPT = F32Layout<LOGN, BLOCK, PAIRS>::kMPT;
+  constexpr bool R16 = PLAN == kPlanRadix16;
+  using L = F32Layout<LOGN, BLOCK, PLAN>;
+  constexpr int MPT = L::kMPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cf* Z0 = reinterpret_cast<cf*>(smem_raw);
   cf* Z1 = Z0 + padded_len<T>(N);
   cf* TW = Z1 + padded_len<T>(N);
-  T* IS = reinterpret_cast<T*>(TW + twiddle_count(LOGN));
+  T* IS = reinterpret_cast<T*>(TW + L::kTwiddles);
   T* SS = IS + K1;
-  constexpr bool kSmemState = F32Layout<LOGN, BLOCK, PAIRS>::kSmemState;
+  constexpr bool kSmemState = L::kSmemState;
   cf* NUS = reinterpret_cast<cf*>(SS + K1);  // kSmemState: N(u), a1, acc in shared memory, [3][3][K1]
 
   cf u[MPT][3], ulo[MPT][3], nu[MPT][3], a1[MPT][3], acc[MPT][3], acclo[MPT][3];
   const cd* src = in + (size_t)slice * 3 * H;
-  for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TW[t] = tb.tw[t];
+  const cf* twg = R16 ? tb.tw16 : tb.tw;
+  for (int t = threadIdx.x; t < L::kTwiddles; t += BLOCK) TW[t] = twg[t];
 #pragma unroll
   for (int r = 0; r < MPT; ++r) {
     const int k = threadIdx.x + r * BLOCK;
@@ -416,11 +432,11 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
         u[r][q] = cvt<float>(a[q]);
         ulo[r][q] = cvt<float>(a[q] - cvt<double>(u[r][q]));
       }
-      pack_mode<T, N>(Z0, Z1, k, u[r], is, ss);
+      pack_mode<T, N, R16>(Z0, Z1, k, u[r], is, ss);
     }
   }
   for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK)
-    if (k > K) zero_mode<T, N>(Z0, Z1, k);
+    if (k > K) zero_mode<T, N, R16>(Z0, Z1, k);
   __syncthreads();
 
   const EtdView<T> e = tb.etd;
@@ -429,7 +445,9 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
     const bool last = (step == steps - 1);
 #pragma unroll 1
     for (int stage = 0; stage < 4; ++stage) {
-      if constexpr (PAIRS)
+      if constexpr (PLAN == kPlanRadix16)
+        nonlinear_transform16<LOGN, BLOCK>(Z0, TW);  // lanes Z0, Z1 = Z0 + N
+      else if constexpr (PLAN == kPlanPairs)
         nonlinear_transform_pairs<T, LOGN, BLOCK>(Z0, 1, TW);  // lanes Z0, Z1 = Z0 + padded_len
       else
         nonlinear_transform<T, LOGN, BLOCK>(Z0, 1, TW);
@@ -440,7 +458,7 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
         if (k > K) continue;
         const T is = IS[k], ss = SS[k];
         cf bn[3], nx[3];
-        unpack_mode<T, N>(Z0, Z1, k, is, ss, bn);
+        unpack_mode<T, N, R16>(Z0, Z1, k, is, ss, bn);
         if constexpr (SCHEME == kSchemeEtdrk4) {
           if constexpr (kSmemState)
             etd32_stage3(stage, k, K1, bn, u[r], ulo[r], NUS + k, NUS + 3 * K1 + k, NUS + 6 * K1 + k, K1, tb.etdc, nx);
@@ -477,12 +495,12 @@ __device__ __forceinline__ void fine_f32_body(const cd* __restrict__ in, cd* __r
             }
           }
         }
-        if (pack_next) pack_mode<T, N>(Z0, Z1, k, nx, is, ss);
+        if (pack_next) pack_mode<T, N, R16>(Z0, Z1, k, nx, is, ss);
       }
       if (pack_next)
         // bins above the kept modes, cleared by the threads whose own wavenumber lies there
         for (int k = threadIdx.x; k <= zero_end<N>(); k += BLOCK)
-          if (k > K) zero_mode<T, N>(Z0, Z1, k);
+          if (k > K) zero_mode<T, N, R16>(Z0, Z1, k);
       __syncthreads();
     }
   }
@@ -518,7 +536,14 @@ constexpr int fine_pairs_min_blocks() {
 template <int LOGN, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, fine_pairs_min_blocks<LOGN>())
     fine_sweep_kernel_f32_pairs(const cd* __restrict__ in, cd* __restrict__ out, int steps, FineTabs<float> tb) {
-  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, true>(in, out, steps, tb, blockIdx.x);
+  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, kPlanPairs>(in, out, steps, tb, blockIdx.x);
+}
+
+// The radix-16 schedule: N/8 threads as the lane-pair schedule, and its register bound.
+template <int LOGN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, fine_pairs_min_blocks<LOGN>())
+    fine_sweep_kernel_f32_r16(const cd* __restrict__ in, cd* __restrict__ out, int steps, FineTabs<float> tb) {
+  fine_f32_body<LOGN, BLOCK, kSchemeEtdrk4, kPlanRadix16>(in, out, steps, tb, blockIdx.x);
 }
 
 template <typename T>
@@ -528,27 +553,28 @@ template <>
 inline FineTabs<double> fine_tabs<double>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd64, c->etd64 + n, c->etd64 + 2 * n, c->etd64 + 3 * n, c->etd64 + 4 * n, c->etd64 + 5 * n},
-          nullptr, nullptr, c->tw64, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64, c->h};
+          nullptr, nullptr, c->tw64, nullptr, c->inv_sig64, c->sk_sig64, c->inv_sig64, c->sk_sig64, c->h};
 }
 
 template <>
 inline FineTabs<float> fine_tabs<float>(const arp_ctx* c) {
   const int n = 3 * c->K1;
   return {{c->etd32, c->etd32 + n, c->etd32 + 2 * n, c->etd32 + 3 * n, c->etd32 + 4 * n, c->etd32 + 5 * n},
-          c->E_lo32, c->etd32c, c->tw32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64, c->h};
+          c->E_lo32, c->etd32c, c->tw32, c->tw16_32, c->inv_sig32, c->sk_sig32, c->inv_sig64, c->sk_sig64, c->h};
 }
 
-template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, bool PAIRS = false>
+template <typename T, int LOGN, int BLOCK, int SCHEME = kSchemeEtdrk4, int PLAN = kPlanRadix8>
 arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int steps, cudaStream_t s) {
   constexpr bool kF32 = std::is_same<T, float>::value;
-  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK, PAIRS>::kBytes : FineLayout<T, LOGN>::kBytes;
+  const size_t smem = kF32 ? F32Layout<LOGN, BLOCK, PLAN>::kBytes : FineLayout<T, LOGN>::kBytes;
   const void* kern;
-  if constexpr (PAIRS) kern = (const void*)fine_sweep_kernel_f32_pairs<LOGN, BLOCK>;
+  if constexpr (PLAN == kPlanRadix16) kern = (const void*)fine_sweep_kernel_f32_r16<LOGN, BLOCK>;
+  else if constexpr (PLAN == kPlanPairs) kern = (const void*)fine_sweep_kernel_f32_pairs<LOGN, BLOCK>;
   else if constexpr (kF32) kern = (const void*)fine_sweep_kernel_f32<LOGN, BLOCK, SCHEME>;
   else kern = (const void*)fine_sweep_kernel<T, LOGN, BLOCK, SCHEME>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory attribute");
-  if constexpr (PAIRS) {
+  if constexpr (PLAN != kPlanRadix8) {
     // several such blocks per SM need the largest shared-memory carveout
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return check_cuda(c, e, "fine: shared-memory carveout");
@@ -560,7 +586,8 @@ arp_status launch_fine_block(arp_ctx* c, const cd* in, cd* out, int batch, int s
 }
 
 // The FP32 fine sweep's schedule: 1 = N/4 threads, 2 = N/2 threads, 3 = the
-// lane-pair schedule with N/8 threads (ETDRK4, N >= 256).  ARP_OPT_FINE_BLOCK
+// lane-pair schedule with N/8 threads (ETDRK4, N >= 256), 4 = the radix-16
+// plan with N/8 threads (ETDRK4, 512 <= N <= 2048).  ARP_OPT_FINE_BLOCK
 // of context c if set, else the offline-tuned tables (fine_schedule.h, written
 // by the project's tuner from timings on GB300): the throughput table when the
 // context's slices fill the device (at least two per SM, so every level's fine
@@ -574,8 +601,12 @@ template <int LOGN, int SCHEME = kSchemeEtdrk4>
 int fine_schedule_f32(const arp_ctx* c) {
   const bool fills = c->num_sms > 0 && c->slices >= 2 * c->num_sms;
   const int tuned = fills ? kFineScheduleF32Tp[LOGN] : kFineScheduleF32Lat[LOGN];
+  const bool etd = SCHEME == kSchemeEtdrk4;
+  auto applies = [&](int x) {
+    return x == 1 || x == 2 || (x == 3 && etd && fine_pairs_available(LOGN)) || (x == 4 && etd && r16_available(LOGN));
+  };
   int v = c->fine_block != 0 ? c->fine_block : tuned;
-  if (v == 3 && !(fine_pairs_available(LOGN) && SCHEME == kSchemeEtdrk4)) v = tuned == 3 ? 1 : tuned;
+  if (!applies(v)) v = applies(tuned) ? tuned : 1;
   if (v == 2 && FineBlock<LOGN>::value == FineBlockAlt<LOGN>::value) v = 1;
   return v;
 }
@@ -585,9 +616,15 @@ arp_status launch_fine_n(arp_ctx* c, const cd* in, cd* out, int batch, cudaStrea
   constexpr int B0 = FineBlock<LOGN>::value, B1 = FineBlockAlt<LOGN>::value;
   if constexpr (std::is_same<T, float>::value) {
     const int v = fine_schedule_f32<LOGN, SCHEME>(c);
+    if constexpr (r16_available(LOGN) && SCHEME == kSchemeEtdrk4) {
+      if (v == 4)
+        return launch_fine_block<T, LOGN, FinePairBlock<LOGN>::value, SCHEME, kPlanRadix16>(c, in, out, batch,
+                                                                                          c->steps, s);
+    }
     if constexpr (fine_pairs_available(LOGN) && SCHEME == kSchemeEtdrk4) {
       if (v == 3)
-        return launch_fine_block<T, LOGN, FinePairBlock<LOGN>::value, SCHEME, true>(c, in, out, batch, c->steps, s);
+        return launch_fine_block<T, LOGN, FinePairBlock<LOGN>::value, SCHEME, kPlanPairs>(c, in, out, batch,
+                                                                                        c->steps, s);
     }
     if constexpr (B0 != B1) {
       if (v == 2) return launch_fine_block<T, LOGN, B1, SCHEME>(c, in, out, batch, c->steps, s);

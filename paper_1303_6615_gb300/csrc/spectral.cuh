@@ -94,6 +94,17 @@ __host__ __device__ constexpr int padded_len(int n) {
   return swizzled_lanes<T>(n) ? n : n + (n >> Pad<T>::kShift);
 }
 
+// Lane layout of the radix-16 plan (FP32, 512 <= N <= 2048, spectral16.cuh):
+// element i at i ^ (bits 4-7 of i), no padding.
+__host__ __device__ __forceinline__ constexpr int pidx16(int i) { return i ^ ((i >> 4) & 15); }
+
+// Position of element i of an N-point lane: pidx, or pidx16 for the radix-16 plan's lanes.
+template <typename T, int N, bool R16>
+__host__ __device__ __forceinline__ constexpr int lane_pos(int i) {
+  if constexpr (R16) return pidx16(i);
+  else return pidx<T, N>(i);
+}
+
 // S(bits 4-6 of i): the swizzle term of pidx for swizzled lanes.
 __host__ __device__ __forceinline__ constexpr int swz_term(int i) {
   return (int)((0xCFA95630u >> (((unsigned)i >> 2) & 28u)) & 15u);
@@ -143,8 +154,9 @@ __host__ __device__ constexpr int twiddle_offset(int logn, int logL) {
 __host__ __device__ constexpr int twiddle_count(int logn) { return twiddle_offset(logn, stage_log_mid(logn)); }
 
 // Writes the inverse-transform input of wavenumber k (0 <= k <= K) for the
-// eigen amplitudes a: Z0 = v1 + i h, Z1 = v1_x + i v2_x at bins k and N-k.
-template <typename T, int N>
+// eigen amplitudes a: Z0 = v1 + i h, Z1 = v1_x + i v2_x at bins k and N-k
+// (R16: in the radix-16 plan's lane layout; likewise for zero_mode and unpack_mode).
+template <typename T, int N, bool R16 = false>
 __device__ __forceinline__ void pack_mode(cpx<T>* Z0, cpx<T>* Z1, int k, const cpx<T> a[3], T is, T ss) {
   cpx<T> u[3];
   eigen_to_phys(a, is, ss, u);
@@ -158,26 +170,26 @@ __device__ __forceinline__ void pack_mode(cpx<T>* Z0, cpx<T>* Z1, int k, const c
     Z0[0] = mk<T>(A.x, D.x);
     Z1[0] = mk<T>((T)0, (T)0);
   } else {
-    Z0[pidx<T, N>(k)] = A + mul_i(D);
-    Z0[pidx<T, N>(N - k)] = conj(A) + mul_i(conj(D));
-    Z1[pidx<T, N>(k)] = B + mul_i(C);
-    Z1[pidx<T, N>(N - k)] = conj(B) + mul_i(conj(C));
+    Z0[lane_pos<T, N, R16>(k)] = A + mul_i(D);
+    Z0[lane_pos<T, N, R16>(N - k)] = conj(A) + mul_i(conj(D));
+    Z1[lane_pos<T, N, R16>(k)] = B + mul_i(C);
+    Z1[lane_pos<T, N, R16>(N - k)] = conj(B) + mul_i(conj(C));
   }
 }
 
 // Zeroes bins k and N-k (K < k <= N/2).
-template <typename T, int N>
+template <typename T, int N, bool R16 = false>
 __device__ __forceinline__ void zero_mode(cpx<T>* Z0, cpx<T>* Z1, int k) {
   const cpx<T> z = mk<T>(0, 0);
-  Z0[pidx<T, N>(k)] = z;
-  Z1[pidx<T, N>(k)] = z;
-  Z0[pidx<T, N>(N - k)] = z;
-  Z1[pidx<T, N>(N - k)] = z;
+  Z0[lane_pos<T, N, R16>(k)] = z;
+  Z1[lane_pos<T, N, R16>(k)] = z;
+  Z0[lane_pos<T, N, R16>(N - k)] = z;
+  Z1[lane_pos<T, N, R16>(N - k)] = z;
 }
 
 // Reads the forward-transform output at wavenumber k (0 <= k <= K) and returns
 // the eigen amplitudes b = R^H N_k of the nonlinearity.
-template <typename T, int N>
+template <typename T, int N, bool R16 = false>
 __device__ __forceinline__ void unpack_mode(const cpx<T>* Z0, const cpx<T>* Z1, int k, T is, T ss, cpx<T> b[3]) {
   const T inv_n = (T)1 / (T)N;
   cpx<T> n3[3];
@@ -187,9 +199,9 @@ __device__ __forceinline__ void unpack_mode(const cpx<T>* Z0, const cpx<T>* Z1, 
     n3[1] = mk<T>(q.y * inv_n, 0);
     n3[2] = mk<T>(0, 0);
   } else {
-    cpx<T> q = Z0[pidx<T, N>(k)];
-    cpx<T> qm = conj(Z0[pidx<T, N>(N - k)]);
-    cpx<T> r = Z1[pidx<T, N>(k)];
+    cpx<T> q = Z0[lane_pos<T, N, R16>(k)];
+    cpx<T> qm = conj(Z0[lane_pos<T, N, R16>(N - k)]);
+    cpx<T> r = Z1[lane_pos<T, N, R16>(k)];
     const T half_n = (T)0.5 * inv_n;
     n3[0] = half_n * (q + qm);
     n3[1] = half_n * mul_mi(q - qm);

@@ -1,7 +1,8 @@
 // tables.cu -- per-context tables, computed on the device in FP64 and rounded
 // for the FP32 path:
 //   * eigenvector constants of L_k (Sec. 6.1);
-//   * per-stage FFT twiddles e^{-2 pi i q j / L} of the radix-8 stages;
+//   * per-stage FFT twiddles e^{-2 pi i q j / L} of the radix-8 stages, and of
+//     the radix-16 stages of the FP32 sweep's radix-16 plan;
 //   * ETDRK4 coefficients (Cox & Matthews) per wavenumber and eigen-branch for
 //     the linear symbol lambda = -i omega/eps - nu k^4 (omega = alpha sigma_k);
 //   * time-average nodes' phases e^{-i omega s_m}, s_m = T0 m/M, and weights
@@ -13,6 +14,7 @@
 
 #include "context.h"
 #include "spectral.cuh"
+#include "spectral16.cuh"
 
 namespace arp {
 namespace {
@@ -88,6 +90,24 @@ __global__ void twiddle_kernel(int logn, cd* tw64, cf* tw32) {
   sincospi(-2.0 * (double)(q * j) / (double)(1 << logL), &s, &c);
   tw64[t] = {c, s};
   tw32[t] = {(float)c, (float)s};
+}
+
+// The radix-16 plan's twiddles (FP32 sweep, 512 <= N <= 2048): for each outer
+// stage of span L = 2^logL, entries [(q-1) L/16 + j] = e^{-2 pi i q j / L},
+// q = 1..15, j < L/16.
+__global__ void twiddle16_kernel(int logn, cf* tw16) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= twiddle16_count(logn)) return;
+  int off = 0, logL = logn;
+  while (t >= off + 15 * ((1 << logL) / 16)) {
+    off += 15 * ((1 << logL) / 16);
+    logL -= 4;
+  }
+  const int e = (1 << logL) / 16;
+  const int q = (t - off) / e + 1, j = (t - off) % e;
+  double s, c;
+  sincospi(-2.0 * (double)(q * j) / (double)(1 << logL), &s, &c);
+  tw16[t] = {(float)c, (float)s};
 }
 
 // omega of branch b (alpha = b - 1) at wavenumber k.
@@ -224,6 +244,7 @@ arp_status build_tables(arp_ctx* c, cudaStream_t st) {
   eigen_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->inv_sig64, c->sk_sig64, c->inv_sig32,
                                                            c->sk_sig32);
   twiddle_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw64, c->tw32);
+  if (r16_available(c->logN)) twiddle16_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw16_32);
   etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32,
                                                    c->etd32c);
   weights_kernel<<<1, 256, 0, st>>>(c->M, c->weight64, c->weight32);

@@ -3,7 +3,8 @@
 For every grid size N = 8 .. 2048 it times each schedule of the FP32 ETDRK4
 fine sweep (ARP_OPT_FINE_BLOCK 1 = N/4 threads per slice, 2 = N/2 threads,
 3 = N/8 threads with both FFT lanes per butterfly and the stage values in
-shared memory, where it applies) on one GPU, through the C ABI, in the two
+shared memory, 4 = N/8 threads with radix-16 transform stages and the stage
+values in shared memory, where they apply) on one GPU, through the C ABI, in the two
 regimes the library launches it in: a whole sweep of many slices (--slices,
 several per SM: throughput, as a level-by-level iteration or a batch runs it)
 and a chunk of a few slices (--chunk, well under one per SM: the per-slice
@@ -35,7 +36,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HEADER = os.path.join(PKG, "csrc", "fine_schedule.h")
-SCHEDULES = {1: "N/4 threads", 2: "N/2 threads", 3: "N/8 threads, lane pairs, shared stage values"}
+SCHEDULES = {1: "N/4 threads", 2: "N/2 threads", 3: "N/8 threads, lane pairs, shared stage values",
+             4: "N/8 threads, radix-16 stages, shared stage values"}
 
 
 def schedules_for(logn: int) -> list[int]:
@@ -45,6 +47,8 @@ def schedules_for(logn: int) -> list[int]:
         out.append(2)
     if logn >= 8:
         out.append(3)
+    if 9 <= logn <= 11:
+        out.append(4)
     return out
 
 
@@ -77,7 +81,8 @@ def write_header(tp_table: list[int], lat_table: list[int], times: dict, lat: di
     lines = [
         "// fine_schedule.h -- written by paper_1303_6615_gb300/tune.py; do not edit.",
         "// Default schedules of the FP32 ETDRK4 fine sweep per log2 N (index 0..11):",
-        "// 1 = N/4 threads per slice, 2 = N/2 threads, 3 = N/8 threads with lane pairs.",
+        "// 1 = N/4 threads per slice, 2 = N/2 threads, 3 = N/8 threads with lane pairs,",
+        "// 4 = N/8 threads with radix-16 stages.",
         f"// Measured on {gpu}, {steps} steps, median of 3, ms: a sweep of {slices} slices (throughput)",
         f"// / of {chunk} slices (latency); the fastest of each regime is kept.",
     ]

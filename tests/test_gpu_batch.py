@@ -134,15 +134,16 @@ def test_problem_joining_a_running_batch_and_chain_fallback():
 
 
 
-def test_batched_members_keep_their_fine_block_size():
+@pytest.mark.parametrize("n,opts", [(256, [1, 2, 0, 3]), (512, [4, 3, 0, 1])])
+def test_batched_members_keep_their_fine_block_size(n, opts):
     # Members of one (N, precision) group that ask for different FP32 fine-sweep
     # schedules (ARP_OPT_FINE_BLOCK) each get the iterates of a solo run with
-    # the same option, bit for bit.
+    # the same option, bit for bit (N = 256: schedules 1-3; N = 512: the
+    # radix-16 schedule 4 too).
     torch = cuda_or_skip()
     from paper_1303_6615_gb300 import binding as b
-    base = (256, 1e-2, 1e-4, 4, 0.04, 4e-3, 16, 1, 6)  # N >= 256: all three FP32 schedules apply
-    probs = [base[:8] + (40 + i,) for i in range(4)]
-    opts = [1, 2, 0, 3]
+    base = (n, 1e-2, 1e-4, 4, 0.04, 4e-3, 16, 1, 6)
+    probs = [base[:8] + (40 + i,) for i in range(len(opts))]
     alone = []
     for p, v in zip(probs, opts):
         with b.Solver(*p[:7], precision=p[7]) as s:

@@ -253,29 +253,34 @@ def test_fine_fp32_small_workload_and_large_sample():
 
 @pytest.mark.parametrize("n", [64, 128, 256, 512, 1024, 2048])
 def test_fine_fp32_schedules(n):
-    # The FP32 fine sweep has three schedules (ARP_OPT_FINE_BLOCK 1 = N/4 threads,
+    # The FP32 fine sweep has four schedules (ARP_OPT_FINE_BLOCK 1 = N/4 threads,
     # 2 = N/2 threads, 3 = N/8 threads with lane pairs and shared stage values for
-    # N >= 256; 0 takes the tuned default per grid size).  Each is deterministic,
-    # each meets the FP32 bar against the oracle, they differ only by FP32
-    # rounding, and the default is one of them.
+    # N >= 256, 4 = N/8 threads with radix-16 stages for 512 <= N <= 2048; 0
+    # takes the tuned default per grid size; 3 and 4 fall back to the default
+    # where they do not apply).  Each is deterministic, each meets the FP32 bar
+    # against the oracle, they differ only by FP32 rounding, and the default is
+    # one of them.
     cuda_or_skip()
     from paper_1303_6615_gb300 import binding as b
     p = o.Params(n, 0.02, 1e-4 if n <= 256 else 1e-6, 0.02, 0.002, 8)
     x = _states(n, 5, 300 + n, amp=float(n) * 2.0 if n <= 1024 else 1024.0)
-    got = {}
+    got, sched = {}, {}
     with _solver(p, 5, precision=b.ARP_FP32) as s:
         with pytest.raises(b.ArpError) as ei:
-            b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, 4)
+            b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, 5)
         assert ei.value.status == b.ARP_EINVAL
-        for v in (0, 1, 2, 3):
+        for v in (0, 1, 2, 3, 4):
             b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, v)
+            sched[v] = b.arp_info(s.ctx)["fine_schedule"]
             got[v] = _gpu_call(b.arp_fine_batch, s, x)
             np.testing.assert_array_equal(_gpu_call(b.arp_fine_batch, s, x), got[v])
-    assert any(np.array_equal(got[0], got[v]) for v in (1, 2, 3))
-    for v in (2, 3):
+    assert sched[1] == 1 and sched[3] == (3 if n >= 256 else sched[0])
+    assert sched[4] == (4 if 512 <= n <= 2048 else sched[0])
+    assert any(np.array_equal(got[0], got[v]) for v in (1, 2, 3, 4))
+    for v in (2, 3, 4):
         assert per_state_rel_l2(got[1], got[v]).max() <= 1e-6, v
     ref = o.fine_propagate(x, p)
-    for v in (1, 2, 3):
+    for v in (1, 2, 3, 4):
         assert per_state_rel_l2(got[v], ref).max() <= TOL32, v
 
 
