@@ -38,6 +38,23 @@ using cd = cpx<double>;
 using cf = cpx<float>;
 
 #if defined(__CUDACC__)
+// Sum and difference of two complex values for transform butterflies: FP32 as
+// one packed two-lane FP32 add of the sm_100 family (__fadd2_rn), per
+// component the same correctly rounded add as the scalar one, so results are
+// unchanged while the instruction count halves; FP64 as two scalar adds.
+// Callers use them where neither operand is a bare product, so that no
+// multiply-add contraction of the scalar form is given up.
+__device__ __forceinline__ cpx<float> bsum(cpx<float> a, cpx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  return {r.x, r.y};
+}
+__device__ __forceinline__ cpx<float> bdif(cpx<float> a, cpx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(-b.x, -b.y));
+  return {r.x, r.y};
+}
+__device__ __forceinline__ cpx<double> bsum(cpx<double> a, cpx<double> b) { return a + b; }
+__device__ __forceinline__ cpx<double> bdif(cpx<double> a, cpx<double> b) { return a - b; }
+
 // Unevaluated float pair hi + lo (|lo| <= ulp(hi)/2): about 48 significant
 // bits from FP32 arithmetic, using the error-free transforms of Knuth
 // (two-sum), Dekker (fast two-sum) and the FMA product error.

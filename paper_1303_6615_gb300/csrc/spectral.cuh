@@ -210,32 +210,37 @@ __device__ __forceinline__ void unpack_mode(const cpx<T>* Z0, const cpx<T>* Z1, 
   phys_to_eigen(n3, is, ss, b);
 }
 
-// Length-4 DFT with root e^{sign 2 pi i/4} = sign * i.
-template <typename T, int SIGN>
+// Length-4 DFT with root e^{sign 2 pi i/4} = sign * i.  P02 / P13: the pair
+// (x0, x2) / (x1, x3) may use the packed butterfly adds (bsum, bdif), i.e.
+// neither of its entries is a bare product; the second level's operands are
+// sums and always may.  A product by +-i swaps components and stays scalar.
+template <typename T, int SIGN, bool P02 = true, bool P13 = true>
 __device__ __forceinline__ void dft4(cpx<T>& x0, cpx<T>& x1, cpx<T>& x2, cpx<T>& x3) {
-  cpx<T> a0 = x0 + x2, a1 = x0 - x2, a2 = x1 + x3;
-  cpx<T> a3 = SIGN > 0 ? mul_i(x1 - x3) : mul_mi(x1 - x3);
-  x0 = a0 + a2;
-  x2 = a0 - a2;
+  const cpx<T> a0 = P02 ? bsum(x0, x2) : x0 + x2, a1 = P02 ? bdif(x0, x2) : x0 - x2;
+  const cpx<T> a2 = P13 ? bsum(x1, x3) : x1 + x3, d = P13 ? bdif(x1, x3) : x1 - x3;
+  const cpx<T> a3 = SIGN > 0 ? mul_i(d) : mul_mi(d);
+  x0 = bsum(a0, a2);
+  x2 = bdif(a0, a2);
   x1 = a1 + a3;
   x3 = a1 - a3;
 }
 
 // Length-8 DFT with root w = e^{sign 2 pi i/8}: two length-4 DFTs of the even
 // and odd entries, combined with w^1 = (1 + sign i)/sqrt2, w^2 = sign i,
-// w^3 = (-1 + sign i)/sqrt2.
-template <typename T, int SIGN>
+// w^3 = (-1 + sign i)/sqrt2.  PACK: the inputs are no bare products (see dft4);
+// the combination's products by w^1, w^3 keep their scalar (contractible) adds.
+template <typename T, int SIGN, bool PACK = true>
 __device__ __forceinline__ void dft8(cpx<T> x[8]) {
   cpx<T> e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
   cpx<T> o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-  dft4<T, SIGN>(e0, e1, e2, e3);
-  dft4<T, SIGN>(o0, o1, o2, o3);
+  dft4<T, SIGN, PACK, PACK>(e0, e1, e2, e3);
+  dft4<T, SIGN, PACK, PACK>(o0, o1, o2, o3);
   const T r = Consts<T>::rsqrt2();
   const cpx<T> t1 = SIGN > 0 ? r * (o1 + mul_i(o1)) : r * (o1 - mul_i(o1));
   const cpx<T> t2 = SIGN > 0 ? mul_i(o2) : mul_mi(o2);
   const cpx<T> t3 = SIGN > 0 ? r * (mul_i(o3) - o3) : r * (mk<T>(-o3.x, -o3.y) - mul_i(o3));
-  x[0] = e0 + o0;
-  x[4] = e0 - o0;
+  x[0] = bsum(e0, o0);
+  x[4] = bdif(e0, o0);
   x[1] = e1 + t1;
   x[5] = e1 - t1;
   x[2] = e2 + t2;
@@ -248,18 +253,18 @@ __device__ __forceinline__ void dft8(cpx<T> x[8]) {
 // a2 = x[7], a3 = -(sign i) x[7]; the rest as dft8 (the same roundings).
 template <typename T, int SIGN>
 __device__ __forceinline__ void dft8_in34zero(cpx<T> x[8]) {
-  const cpx<T> ea2 = x[2] + x[6];
-  const cpx<T> ea3 = SIGN > 0 ? mul_i(x[2] - x[6]) : mul_mi(x[2] - x[6]);
-  const cpx<T> e0 = x[0] + ea2, e2 = x[0] - ea2, e1 = x[0] + ea3, e3 = x[0] - ea3;
-  const cpx<T> oa0 = x[1] + x[5], oa1 = x[1] - x[5];
+  const cpx<T> ea2 = bsum(x[2], x[6]);
+  const cpx<T> ea3 = SIGN > 0 ? mul_i(bdif(x[2], x[6])) : mul_mi(bdif(x[2], x[6]));
+  const cpx<T> e0 = bsum(x[0], ea2), e2 = bdif(x[0], ea2), e1 = x[0] + ea3, e3 = x[0] - ea3;
+  const cpx<T> oa0 = bsum(x[1], x[5]), oa1 = bdif(x[1], x[5]);
   const cpx<T> oa3 = SIGN > 0 ? mul_mi(x[7]) : mul_i(x[7]);
-  const cpx<T> o0 = oa0 + x[7], o2 = oa0 - x[7], o1 = oa1 + oa3, o3 = oa1 - oa3;
+  const cpx<T> o0 = bsum(oa0, x[7]), o2 = bdif(oa0, x[7]), o1 = oa1 + oa3, o3 = oa1 - oa3;
   const T r = Consts<T>::rsqrt2();
   const cpx<T> t1 = SIGN > 0 ? r * (o1 + mul_i(o1)) : r * (o1 - mul_i(o1));
   const cpx<T> t2 = SIGN > 0 ? mul_i(o2) : mul_mi(o2);
   const cpx<T> t3 = SIGN > 0 ? r * (mul_i(o3) - o3) : r * (mk<T>(-o3.x, -o3.y) - mul_i(o3));
-  x[0] = e0 + o0;
-  x[4] = e0 - o0;
+  x[0] = bsum(e0, o0);
+  x[4] = bdif(e0, o0);
   x[1] = e1 + t1;
   x[5] = e1 - t1;
   x[2] = e2 + t2;
@@ -416,17 +421,18 @@ __device__ __forceinline__ void middle_stage(cpx<T>* Z, int npairs) {
       dft4<T, +1>(a[0], a[1], a[2], a[3]);
       dft4<T, +1>(b[0], b[1], b[2], b[3]);
     } else {
-      const cpx<T> s = a[0] + a[1], d = a[0] - a[1], t = b[0] + b[1], u = b[0] - b[1];
+      const cpx<T> s = bsum(a[0], a[1]), d = bdif(a[0], a[1]), t = bsum(b[0], b[1]), u = bdif(b[0], b[1]);
       a[0] = s; a[1] = d; b[0] = t; b[1] = u;
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) products(a[q], b[q]);
+    // the products are bare products: the first forward level keeps scalar adds
     if (R == 8) {
-      dft8<T, -1>(a);
-      dft8<T, -1>(b);
+      dft8<T, -1, false>(a);
+      dft8<T, -1, false>(b);
     } else if (R == 4) {
-      dft4<T, -1>(a[0], a[1], a[2], a[3]);
-      dft4<T, -1>(b[0], b[1], b[2], b[3]);
+      dft4<T, -1, false, false>(a[0], a[1], a[2], a[3]);
+      dft4<T, -1, false, false>(b[0], b[1], b[2], b[3]);
     } else {
       const cpx<T> s = a[0] + a[1], d = a[0] - a[1], t = b[0] + b[1], u = b[0] - b[1];
       a[0] = s; a[1] = d; b[0] = t; b[1] = u;

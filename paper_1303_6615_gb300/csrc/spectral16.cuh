@@ -48,12 +48,13 @@ __device__ __forceinline__ void dft16(cf x[16]) {
     const cf x0 = z0 ? mk<float>(0.f, 0.f) : x[n2], x1 = z1 ? mk<float>(0.f, 0.f) : x[4 + n2];
     const cf x2 = z2 ? mk<float>(0.f, 0.f) : x[8 + n2], x3 = z3 ? mk<float>(0.f, 0.f) : x[12 + n2];
     // the sums and differences of a DFT of 4, dropping the terms that are zero
-    const cf e0 = z2 ? x0 : (z0 ? x2 : x0 + x2), e1 = z2 ? x0 : (z0 ? mk<float>(-x2.x, -x2.y) : x0 - x2);
-    const cf o0 = z3 ? x1 : (z1 ? x3 : x1 + x3);
-    const cf od = z3 ? x1 : (z1 ? mk<float>(-x3.x, -x3.y) : x1 - x3);
+    // (packed adds: the inputs are loads or twiddle products ending in an FMA)
+    const cf e0 = z2 ? x0 : (z0 ? x2 : bsum(x0, x2)), e1 = z2 ? x0 : (z0 ? mk<float>(-x2.x, -x2.y) : bdif(x0, x2));
+    const cf o0 = z3 ? x1 : (z1 ? x3 : bsum(x1, x3));
+    const cf od = z3 ? x1 : (z1 ? mk<float>(-x3.x, -x3.y) : bdif(x1, x3));
     const cf o1 = SIGN > 0 ? mul_i(od) : mul_mi(od);
-    a[n2][0] = e0 + o0;
-    a[n2][2] = e0 - o0;
+    a[n2][0] = bsum(e0, o0);
+    a[n2][2] = bdif(e0, o0);
     a[n2][1] = e1 + o1;
     a[n2][3] = e1 - o1;
   }
@@ -73,14 +74,18 @@ __device__ __forceinline__ void dft16(cf x[16]) {
   a[3][1] = w3(a[3][1]);
   a[3][2] = w6(a[3][2]);
   a[3][3] = w9(a[3][3]);
+  // DFTs of 4 over n2; a pair keeps scalar adds where an entry is a bare
+  // product (w^2, w^6: their adds contract) or a swap (w^4)
+  dft4<float, SIGN, true, true>(a[0][0], a[1][0], a[2][0], a[3][0]);
+  dft4<float, SIGN, false, true>(a[0][1], a[1][1], a[2][1], a[3][1]);
+  dft4<float, SIGN, false, false>(a[0][2], a[1][2], a[2][2], a[3][2]);
+  dft4<float, SIGN, false, true>(a[0][3], a[1][3], a[2][3], a[3][3]);
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
-    cf y0 = a[0][k1], y1 = a[1][k1], y2 = a[2][k1], y3 = a[3][k1];
-    dft4<float, SIGN>(y0, y1, y2, y3);
-    x[k1] = y0;
-    x[k1 + 4] = y1;
-    x[k1 + 8] = y2;
-    x[k1 + 12] = y3;
+    x[k1] = a[0][k1];
+    x[k1 + 4] = a[1][k1];
+    x[k1 + 8] = a[2][k1];
+    x[k1 + 12] = a[3][k1];
   }
 }
 
@@ -165,17 +170,18 @@ __device__ __forceinline__ void middle16_stage(cf* Z) {
       dft4<float, +1>(a[0], a[1], a[2], a[3]);
       dft4<float, +1>(b[0], b[1], b[2], b[3]);
     } else {
-      const cf s = a[0] + a[1], d = a[0] - a[1], t = b[0] + b[1], u = b[0] - b[1];
+      const cf s = bsum(a[0], a[1]), d = bdif(a[0], a[1]), t = bsum(b[0], b[1]), u = bdif(b[0], b[1]);
       a[0] = s; a[1] = d; b[0] = t; b[1] = u;
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) products(a[q], b[q]);
+    // the products are bare products: the first forward level keeps scalar adds
     if constexpr (R == 8) {
-      dft8<float, -1>(a);
-      dft8<float, -1>(b);
+      dft8<float, -1, false>(a);
+      dft8<float, -1, false>(b);
     } else if constexpr (R == 4) {
-      dft4<float, -1>(a[0], a[1], a[2], a[3]);
-      dft4<float, -1>(b[0], b[1], b[2], b[3]);
+      dft4<float, -1, false, false>(a[0], a[1], a[2], a[3]);
+      dft4<float, -1, false, false>(b[0], b[1], b[2], b[3]);
     } else {
       const cf s = a[0] + a[1], d = a[0] - a[1], t = b[0] + b[1], u = b[0] - b[1];
       a[0] = s; a[1] = d; b[0] = t; b[1] = u;
