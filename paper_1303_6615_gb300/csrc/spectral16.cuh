@@ -106,14 +106,16 @@ __device__ __forceinline__ void butterfly16_positions(int base, int at[16]) {
 // DFT then multiply by conj(tw); DIT (forward, sign -): multiply by tw, then
 // DFT; tw[(q-1) L/16 + j] = e^{-2 pi i q j / L}.  PRUNE 1: inputs q = 6..9 are
 // zero and not read; PRUNE 2: outputs q = 6..9 of lane 0 and q >= 6 of lane 1
-// are not stored.
-template <int N, int BLOCK, int SIGN, bool DIF, int LOGL, int PRUNE = 0>
+// are not stored.  Items: lane-major (item = lane N/16 + butterfly), or
+// GROUPED: warp w takes butterflies 16w .. 16w+15 of both lanes (one per
+// half-warp), which at span N/16 are the points 256w .. 256w+255.
+template <int N, int BLOCK, int SIGN, bool DIF, int LOGL, int PRUNE = 0, bool GROUPED = false>
 __device__ __forceinline__ void radix16_stage(cf* Z, const cf* tw) {
   constexpr int NB = N / 16;
   constexpr int E = 1 << (LOGL - 4);
   for (int item = threadIdx.x; item < 2 * NB; item += BLOCK) {
-    const int lane = item / NB;
-    const int bidx = item - lane * NB;
+    const int lane = GROUPED ? (item >> 4) & 1 : item / NB;
+    const int bidx = GROUPED ? ((item >> 5) << 4) | (item & 15) : item - lane * NB;
     cf* Zl = Z + lane * N;
     const int j = bidx & (E - 1);
     const int base = ((bidx >> (LOGL - 4)) << LOGL) + j;
@@ -145,15 +147,22 @@ __device__ __forceinline__ void radix16_stage(cf* Z, const cf* tw) {
   }
 }
 
-// The middle stage (span R = 2^(log2 N mod 4), twiddles 1) on both lanes:
-// last inverse DFT, products, first forward DFT on the same R positions.
+// The middle stage (span R = 2^(log2 N mod 4) = N/256, twiddles 1) on both
+// lanes: last inverse DFT, products, first forward DFT on the same R
+// positions.  With N/8 threads, warp w takes the items of points 256w ..
+// 256w+255, the points its own GROUPED span-N/16 stages read and write, so
+// only the warp synchronises around this stage.
 template <int LOGN, int BLOCK>
 __device__ __forceinline__ void middle16_stage(cf* Z) {
   constexpr int N = 1 << LOGN;
   constexpr int R = 1 << r16_log_mid(LOGN);
+  static_assert(BLOCK == N / 8 && R == N / 256, "one warp per 256 points");
   cf* Z0 = Z;
   cf* Z1 = Z + N;
-  for (int i = threadIdx.x; i < N / R; i += BLOCK) {
+  const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < 8 / R; ++r) {
+    const int i = (256 / R) * w + t + 32 * r;
     // q < R <= 8 sets only bits below those of R i and below bit 4, so
     // pidx16(R i + q) = pidx16(R i) ^ q
     const int p0 = pidx16(R * i);
@@ -201,13 +210,15 @@ __device__ __forceinline__ void nonlinear_transform16(cf* Z, const cf* TW) {
   constexpr int N = 1 << LOGN;
   constexpr int MID = r16_log_mid(LOGN);
   static_assert(LOGN - 8 == MID, "two radix-16 stages and a middle stage");
+  static_assert(BLOCK == N / 8, "one radix-16 butterfly per thread");
   radix16_stage<N, BLOCK, +1, true, LOGN, 1>(Z, TW + twiddle16_offset(LOGN, LOGN));
   __syncthreads();
-  radix16_stage<N, BLOCK, +1, true, LOGN - 4>(Z, TW + twiddle16_offset(LOGN, LOGN - 4));
-  __syncthreads();
+  // span N/16, middle and span N/16 again touch each warp's own 256 points
+  radix16_stage<N, BLOCK, +1, true, LOGN - 4, 0, true>(Z, TW + twiddle16_offset(LOGN, LOGN - 4));
+  __syncwarp();
   middle16_stage<LOGN, BLOCK>(Z);
-  __syncthreads();
-  radix16_stage<N, BLOCK, -1, false, LOGN - 4>(Z, TW + twiddle16_offset(LOGN, LOGN - 4));
+  __syncwarp();
+  radix16_stage<N, BLOCK, -1, false, LOGN - 4, 0, true>(Z, TW + twiddle16_offset(LOGN, LOGN - 4));
   __syncthreads();
   radix16_stage<N, BLOCK, -1, false, LOGN, 2>(Z, TW + twiddle16_offset(LOGN, LOGN));
   __syncthreads();
