@@ -50,8 +50,8 @@ CPU_SAMPLE_SLICES = 8           # cpu_baseline sample, one core (about 10-20 s o
 CPU_PARALLEL_SLICES_PER_CORE = 2  # cpu_baseline sample in parallel over slices: slices per host core
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the fine-sweep kernel on a workload
 # (ncu capture of the current kernel); None where no capture of the current kernel exists.
-FINE_TRAFFIC_BYTES = {("rsw-N1024-eps1e-4-S512-M128", "fp32", 3): 8725760,   # fine_sweep_kernel_f32_pairs<10,128>
-                      ("rsw-N1024-eps1e-4-S512-M128", "fp32", 4): None,      # fine_sweep_kernel_f32_r16<10,128>
+FINE_TRAFFIC_BYTES = {("rsw-N1024-eps1e-4-S512-M128", "fp32", 3): None,      # fine_sweep_kernel_f32_pairs<10,128>
+                      ("rsw-N1024-eps1e-4-S512-M128", "fp32", 4): 8689408,   # fine_sweep_kernel_f32_r16<10,128>
                       ("rsw-N512-eps1e-3-S256-M64", "fp32", 2): 2256896}     # fine_sweep_kernel_f32<9,256>
 REFERENCE_SAMPLE_SLICES = 2     # per-step sample of the reference arm
 
@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--instances", type=int, default=1024)
     ap.add_argument("--kernels-workload", choices=["n1024", "n512"], default="n1024",
                     help="with --mode kernels: the N=1024 headline workload or the N=512 instance")
+    ap.add_argument("--fine-block", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="with --mode kernels: the FP32 fine sweep's schedule (ARP_OPT_FINE_BLOCK; 0 = tuned)")
     ap.add_argument("--probe", action="store_true",
                     help="with --mode dftgemm: only one small time average (a case sized for a profiler)")
     return ap.parse_args()
@@ -1149,6 +1151,7 @@ def run_kernels(args) -> dict:
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
         b.arp_set_option(s.ctx, b.ARP_OPT_PIPELINE, 0)
+        b.arp_set_option(s.ctx, b.ARP_OPT_FINE_BLOCK, args.fine_block)
         u0 = torch.from_numpy(w.initial_state()).cuda()
         for timed in (False, True):
             b.arp_set_initial(s.ctx, u0)
@@ -1162,7 +1165,9 @@ def run_kernels(args) -> dict:
         k, ch = b.arp_parareal_iterate(s.ctx)
         ev[2].record()
         torch.cuda.synchronize()
-    return {"mode": "kernels", "workload": w.name, "precision": args.precision, "level": k, "change": ch,
+        sched = b.arp_info(s.ctx)["fine_schedule"]
+    return {"mode": "kernels", "workload": w.name, "precision": args.precision, "fine_schedule": sched,
+            "level": k, "change": ch,
             "predictor_ms": ev[0].elapsed_time(ev[1]), "iteration_ms": ev[1].elapsed_time(ev[2]),
             "note": "one timed pass after one warm-up pass; a case for profilers, not the benchmark"}
 
