@@ -244,7 +244,10 @@ arp_status build_tables(arp_ctx* c, cudaStream_t st) {
   eigen_consts_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, c->inv_sig64, c->sk_sig64, c->inv_sig32,
                                                            c->sk_sig32);
   twiddle_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw64, c->tw32);
-  if (r16_available(c->logN)) twiddle16_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw16_32);
+  // only a context's own allocation has the FP32 sweep's radix-16 table (the
+  // allocation-free time average, which builds its tables in a static array, has none)
+  if (r16_available(c->logN) && c->tw16_32)
+    twiddle16_kernel<<<(c->N + tb - 1) / tb, tb, 0, st>>>(c->logN, c->tw16_32);
   etd_kernel<<<(c->K1 + tb - 1) / tb, tb, 0, st>>>(c->K1, s, inv_eps, c->nu, c->h, c->etd64, c->etd32, c->E_lo32,
                                                    c->etd32c);
   weights_kernel<<<1, 256, 0, st>>>(c->M, c->weight64, c->weight32);
