@@ -21,16 +21,46 @@ def _call(fn, s, x):
 
 
 def test_sweep_workload_sampled():
+    # Two states of the N = 1024 workload (1954 steps, M = 128) through contexts
+    # of 2 slices and of the workload's 512 slices: the schedule tables pick the
+    # FP32 fine sweep by the context's slices per SM, so the 512-slice context
+    # runs the schedule the benchmark's sweeps run.
     cuda_or_skip()
     from paper_1303_6615_gb300 import binding as b
     w = ri.SWEEP_N1024
     p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
     x = ri.random_batch(w.n_grid, w.ic_cutoff, w.ic_scale_div, 2, 77) * 64.0
     fine, avg = o.fine_propagate(x, p), o.nbar(x, p)
-    for prec, tol in ((b.ARP_FP64, 1e-10), (b.ARP_FP32, 1e-5)):
-        with b.Solver(w.n_grid, w.eps, w.nu, 2, w.dT, w.dt, w.m_quad, precision=prec) as s:
-            assert per_state_rel_l2(_call(b.arp_fine_batch, s, x), fine).max() <= tol, prec
-            assert per_state_rel_l2(_call(b.arp_coarse_avg, s, x), avg).max() <= tol, prec
+    for prec, tol, slices in ((b.ARP_FP64, 1e-10, 2), (b.ARP_FP32, 1e-5, 2), (b.ARP_FP32, 1e-5, w.slices)):
+        with b.Solver(w.n_grid, w.eps, w.nu, slices, w.dT, w.dt, w.m_quad, precision=prec) as s:
+            assert per_state_rel_l2(_call(b.arp_fine_batch, s, x), fine).max() <= tol, (prec, slices)
+            assert per_state_rel_l2(_call(b.arp_coarse_avg, s, x), avg).max() <= tol, (prec, slices)
+
+
+def test_headline_solve_finite_termination():
+    # The benchmark's own call on the N = 1024 workload (512 slices, FP32 bulk,
+    # arp_parareal_solve with K_max 5, pipelined where the device allows):
+    # after k iterations parareal reproduces the serial fine solution exactly
+    # on slices n <= k (Sec. 3), a property that holds at any size, so slices
+    # 1..5 must equal F^n(u0) of the oracle within the FP32 bar.
+    torch = cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    w = ri.SWEEP_N1024
+    p = o.Params(w.n_grid, w.eps, w.nu, w.dT, w.dt, w.m_quad)
+    u0 = w.initial_state()
+    with b.Solver(w.n_grid, w.eps, w.nu, w.slices, w.dT, w.dt, w.m_quad, precision=b.ARP_FP32) as s:
+        b.arp_set_option(s.ctx, b.ARP_OPT_KMAX, 5)
+        b.arp_set_initial(s.ctx, to_dev(u0))
+        k, _ = b.arp_parareal_solve(s.ctx)
+        U = torch.empty((w.slices + 1, 3, w.n_grid // 2 + 1), dtype=torch.complex128, device="cuda")
+        b.arp_get_slices(s.ctx, U)
+        got = to_host(U)
+    assert k == 5
+    assert np.all(np.isfinite(got))
+    ref = o.project(u0, w.n_grid)[None]
+    for n in range(1, 6):
+        ref = o.fine_propagate(ref, p)
+        assert per_state_rel_l2(got[n:n + 1], ref).max() <= 1e-5, n
 
 
 def test_uneven_instances_batched():
