@@ -4,15 +4,15 @@
 // 4 = N/8 threads with radix-16 stages.
 // Measured on NVIDIA GB300, 64 steps, median of 3, ms: a sweep of 512 slices (throughput)
 // / of 16 slices (latency); the fastest of each regime is kept.
-//   N =     8  1: 0.184 / 0.172  -> 1 / 1
-//   N =    16  1: 0.251 / 0.241  -> 1 / 1
-//   N =    32  1: 0.265 / 0.255  -> 1 / 1
-//   N =    64  1: 0.267 / 0.251  -> 1 / 1
-//   N =   128  1: 0.368 / 0.336, 2: 0.354 / 0.259  -> 2 / 2
-//   N =   256  1: 0.477 / 0.336, 2: 0.414 / 0.266, 3: 0.581 / 0.521  -> 2 / 2
-//   N =   512  1: 0.897 / 0.364, 2: 0.876 / 0.330, 3: 0.762 / 0.524, 4: 0.822 / 0.576  -> 3 / 2
-//   N =  1024  1: 1.786 / 0.615, 2: 2.435 / 0.626, 3: 1.641 / 0.836, 4: 1.463 / 0.774  -> 4 / 1
-//   N =  2048  1: 3.794 / 0.971, 3: 3.511 / 1.154, 4: 3.106 / 1.034  -> 4 / 1
+//   N =     8  1: 0.183 / 0.174  -> 1 / 1
+//   N =    16  1: 0.246 / 0.238  -> 1 / 1
+//   N =    32  1: 0.266 / 0.256  -> 1 / 1
+//   N =    64  1: 0.258 / 0.249  -> 1 / 1
+//   N =   128  1: 0.365 / 0.333, 2: 0.333 / 0.261  -> 2 / 2
+//   N =   256  1: 0.459 / 0.339, 2: 0.410 / 0.274, 3: 0.559 / 0.508  -> 2 / 2
+//   N =   512  1: 0.881 / 0.363, 2: 0.857 / 0.338, 3: 0.715 / 0.511, 4: 0.759 / 0.539  -> 3 / 2
+//   N =  1024  1: 1.722 / 0.599, 2: 2.430 / 0.623, 3: 1.566 / 0.802, 4: 1.384 / 0.739  -> 4 / 1
+//   N =  2048  1: 3.755 / 0.955, 3: 3.334 / 1.122, 4: 2.957 / 1.036  -> 4 / 1
 #pragma once
 
 namespace arp {
