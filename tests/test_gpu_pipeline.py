@@ -72,6 +72,20 @@ def test_pipelined_solve_is_the_level_by_level_solve(chunk):
     _same(got, ref)
 
 
+@pytest.mark.parametrize("sched", [3, 4])
+def test_pipelined_solve_is_the_level_by_level_solve_n512_schedules(sched):
+    # the shared-state FP32 schedules (lane pairs; radix-16 plan) at N = 512 on a
+    # ragged chunking: pipelined = level by level, bit for bit
+    cuda_or_skip()
+    from paper_1303_6615_gb300 import binding as b
+    p, u0, S = _params(n=512, S=13, m=16)
+    opts = ((b.ARP_OPT_FINE_BLOCK, sched),)
+    ref = _solve(b, p, u0, S, b.ARP_FP32, 0, 3, opts=opts)
+    got = _solve(b, p, u0, S, b.ARP_FP32, 5, 3, opts=opts)
+    assert got[3]["pipelined"] == 1, got[3]
+    _same(got, ref)
+
+
 def test_pipelined_solve_against_the_oracle():
     cuda_or_skip()
     from paper_1303_6615_gb300 import binding as b
