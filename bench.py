@@ -1199,7 +1199,7 @@ def main():
     if out is not None:
         if world == 1 and not args.headline_only:
             # the same solve on the single large instance, the time to 1e-5 and serving latency
-            big = run_ours(args, rank, world, LARGE, timed_steps=min(args.steps, 10))
+            big = run_ours(args, rank, world, LARGE, timed_steps=args.steps)
             out["config_N512"] = {k: big[k] for k in ("value", "unit", "ms_per_step", "config", "roofline", "e2e",
                                                       "level_by_level", "fine_only", "clocks")}
             tts = run_tts(args, LARGE)
