@@ -179,8 +179,8 @@ __device__ __forceinline__ void middle16_stage(cf* Z) {
       dft4<float, +1>(a[0], a[1], a[2], a[3]);
       dft4<float, +1>(b[0], b[1], b[2], b[3]);
     } else {
-      const cf s = bsum(a[0], a[1]), d = bdif(a[0], a[1]), t = bsum(b[0], b[1]), u = bdif(b[0], b[1]);
-      a[0] = s; a[1] = d; b[0] = t; b[1] = u;
+      const cf sa = bsum(a[0], a[1]), da = bdif(a[0], a[1]), sb = bsum(b[0], b[1]), db = bdif(b[0], b[1]);
+      a[0] = sa; a[1] = da; b[0] = sb; b[1] = db;
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) products(a[q], b[q]);
@@ -192,8 +192,8 @@ __device__ __forceinline__ void middle16_stage(cf* Z) {
       dft4<float, -1, false, false>(a[0], a[1], a[2], a[3]);
       dft4<float, -1, false, false>(b[0], b[1], b[2], b[3]);
     } else {
-      const cf s = a[0] + a[1], d = a[0] - a[1], t = b[0] + b[1], u = b[0] - b[1];
-      a[0] = s; a[1] = d; b[0] = t; b[1] = u;
+      const cf sa = a[0] + a[1], da = a[0] - a[1], sb = b[0] + b[1], db = b[0] - b[1];
+      a[0] = sa; a[1] = da; b[0] = sb; b[1] = db;
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
