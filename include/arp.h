@@ -116,8 +116,9 @@ typedef enum {
                                 arp_query_bytes(N_c, slices, M, precision) bytes on first use;
                                 arp_coarse_avg and arp_coarse_step keep the fine grid */
   ARP_OPT_PIPELINE = 11,  /* arp_parareal_solve as a pipeline across iterations: 0 = off (one
-                             level after another), 1 = on with chunks of max(4, ceil(S/16))
-                             links (default), n >= 2 = chunks of n links.  The SMs are split
+                             level after another), 1 = on with chunks of
+                             min(16, max(4, ceil(S/16))) links (default), n >= 2 = chunks
+                             of n links.  The SMs are split
                              into two partitions (green contexts): one that holds the coarse
                              chain's thread-block cluster, one for the fine sweeps, which start
                              on a chunk's slices as soon as the chain has produced their start

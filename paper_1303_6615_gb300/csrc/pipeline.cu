@@ -316,7 +316,7 @@ arp_status ensure_pipe(arp_ctx* c) {
   if (!c->pipe) c->pipe = new Pipe;
   Pipe& p = *c->pipe;
   const int S = c->slices;
-  const int chunk = c->pipeline >= 2 ? std::min(c->pipeline, S) : std::max(4, (S + 15) / 16);
+  const int chunk = c->pipeline >= 2 ? std::min(c->pipeline, S) : std::min(16, std::max(4, (S + 15) / 16));
   if (p.refused) return ARP_OK;
   arp_status r = ARP_OK;
   if (!p.built) {

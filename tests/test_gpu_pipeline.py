@@ -68,7 +68,7 @@ def test_pipelined_solve_is_the_level_by_level_solve(chunk):
     info = got[3]
     assert info["pipelined"] == 1, info
     assert info["chain_sms"] >= info["cluster"] >= 8 and info["fine_sms"] > 0
-    assert info["chunk"] == (min(chunk, S) if chunk >= 2 else max(4, (S + 15) // 16))
+    assert info["chunk"] == (min(chunk, S) if chunk >= 2 else min(16, max(4, (S + 15) // 16)))
     _same(got, ref)
 
 
