@@ -50,6 +50,7 @@
 
 #include "chain_impl.cuh"  // globaltimer_ns, kBarrierTimeoutNs
 #include "coarse_impl.cuh"
+#include "spectral16.cuh"
 
 namespace arp {
 
@@ -126,11 +127,22 @@ template <int LOGN> struct ClusterBlock {
 // Shared memory: the two mbarriers (RED, WS; 16 bytes), FP64 per own wavenumber (w and e^{dT/2 D} gphase for 3
 // branches, dhalf, the two eigen constants), the FFT lanes, twiddles,
 // the node phases [q][3][K1] and weights, WS/ACC/EXCH and the eigen constants.
+// The FP32 chain's transforms use the radix-16 plan at N = 1024 and 2048 (at
+// N = 512 a state's 64 radix-16 butterflies leave it slower than radix 8).
+template <typename T>
+__host__ __device__ constexpr bool chain_r16(int logn) {
+  return sizeof(T) == 4 && r16_available(logn) && logn >= 10;
+}
+template <typename T>
+__host__ __device__ constexpr int chain_twiddles(int logn) {
+  return chain_r16<T>(logn) ? twiddle16_count(logn) : twiddle_count(logn);
+}
+
 template <typename T>
 inline size_t cluster_chain_smem_bytes(int logn, int q, int own, int C, bool ph_smem, bool tmp_smem) {
   const int K1 = ((1 << logn) - 1) / 3 + 1;
   return (size_t)16 + (size_t)6 * own * sizeof(cd) + (size_t)3 * own * sizeof(double) +
-         (size_t)(2 * q * padded_len<T>(1 << logn) + twiddle_count(logn) + (ph_smem ? 3 * q * K1 : 0) + 3 * K1 +
+         (size_t)(2 * q * padded_len<T>(1 << logn) + chain_twiddles<T>(logn) + (ph_smem ? 3 * q * K1 : 0) + 3 * K1 +
                   (tmp_smem ? 3 * q * K1 : 0) + 3 * C * own) *
              sizeof(cpx<T>) +
          (size_t)(2 * K1 + q) * sizeof(T);
@@ -177,7 +189,8 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
   cd* GPH = W64 + 3 * own;                    // [3][own] e^{dT/2 D} e^{-i omega dT/eps}
   cpx<T>* Z = reinterpret_cast<cpx<T>*>(GPH + 3 * own);
   cpx<T>* TW = Z + 2 * q * PL;
-  cpx<T>* PHs = TW + twiddle_count(LOGN);     // [q][3][K1] phases of this CTA's nodes
+  constexpr bool R16 = chain_r16<T>(LOGN);
+  cpx<T>* PHs = TW + chain_twiddles<T>(LOGN);  // [q][3][K1] phases of this CTA's nodes
   cpx<T>* WS = PHs + (a.ph_smem ? 3 * q * K1 : 0);  // [3][K1] state, written by the owners
   const cpx<T>* PH = a.ph_smem ? PHs : tb.avg.phase + (size_t)m0 * 3 * K1;
   cpx<T>* TMP = WS + 3 * K1;                  // [q][3][K1] weighted terms of this CTA's nodes
@@ -189,7 +202,10 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
   T* SS = IS + K1;
   T* WM = SS + K1;                            // [q] weights of this CTA's nodes
 
-  for (int t = threadIdx.x; t < twiddle_count(LOGN); t += BLOCK) TW[t] = tb.tw[t];
+  {
+    const cpx<T>* twg = R16 ? reinterpret_cast<const cpx<T>*>(tb.tw16) : tb.tw;
+    for (int t = threadIdx.x; t < chain_twiddles<T>(LOGN); t += BLOCK) TW[t] = twg[t];
+  }
   for (int k = threadIdx.x; k < K1; k += BLOCK) {
     IS[k] = tb.is[k];
     SS[k] = tb.ss[k];
@@ -266,26 +282,30 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
         const int d = item / ZE1, k = item - d * ZE1;
         cpx<T>* Z0 = Z + 2 * d * PL;
         if (k > K) {
-          zero_mode<T, N>(Z0, Z0 + PL, k);
+          zero_mode<T, N, R16>(Z0, Z0 + PL, k);
           continue;
         }
         cpx<T> x[3];
 #pragma unroll
         for (int b = 0; b < 3; ++b) x[b] = PH[(d * 3 + b) * K1 + k] * WS[b * K1 + k];
-        pack_mode<T, N>(Z0, Z0 + PL, k, x, IS[k], SS[k]);
+        pack_mode<T, N, R16>(Z0, Z0 + PL, k, x, IS[k], SS[k]);
       }
       if (__syncthreads_or(!alive)) {  // a wait of this CTA gave up
         stop = true;
         break;
       }
-      if (nq > 0) nonlinear_transform<T, LOGN, BLOCK>(Z, nq, TW);
+      if constexpr (R16) {
+        if (nq > 0) nonlinear_transform16<LOGN, BLOCK>(reinterpret_cast<cf*>(Z), reinterpret_cast<const cf*>(TW), nq);
+      } else {
+        if (nq > 0) nonlinear_transform<T, LOGN, BLOCK>(Z, nq, TW);
+      }
       if (a.tmp_smem) {
         // weighted, back-rotated term of each (node, wavenumber)
         for (int item = threadIdx.x; item < nq * K1; item += BLOCK) {
           const int d = item / K1, k = item - d * K1;
           cpx<T> bn[3];
           const cpx<T>* Z0 = Z + 2 * d * PL;
-          unpack_mode<T, N>(Z0, Z0 + PL, k, IS[k], SS[k], bn);
+          unpack_mode<T, N, R16>(Z0, Z0 + PL, k, IS[k], SS[k], bn);
 #pragma unroll
           for (int b = 0; b < 3; ++b) TMP[(d * 3 + b) * K1 + k] = WM[d] * (conj(PH[(d * 3 + b) * K1 + k]) * bn[b]);
         }
@@ -306,7 +326,7 @@ __device__ __forceinline__ void chain_cluster_body(const ClusterChainArgs& a, co
           for (int d = 0; d < nq; ++d) {
             cpx<T> bn[3];
             const cpx<T>* Z0 = Z + 2 * d * PL;
-            unpack_mode<T, N>(Z0, Z0 + PL, k, IS[k], SS[k], bn);
+            unpack_mode<T, N, R16>(Z0, Z0 + PL, k, IS[k], SS[k], bn);
 #pragma unroll
             for (int b = 0; b < 3; ++b) s[b] = s[b] + WM[d] * (conj(PH[(d * 3 + b) * K1 + k]) * bn[b]);
           }

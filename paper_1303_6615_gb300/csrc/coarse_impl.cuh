@@ -19,6 +19,7 @@ template <typename T>
 struct NbarTabs {
   AvgView<T> avg;
   const cpx<T>* tw;
+  const cf* tw16;  // FP32, 512 <= N <= 2048: the radix-16 plan's twiddles (the cluster chain)
   const T* is;
   const T* ss;
 };
@@ -117,11 +118,11 @@ template <typename T>
 NbarTabs<T> nbar_tabs(const arp_ctx* c);
 template <>
 inline NbarTabs<double> nbar_tabs<double>(const arp_ctx* c) {
-  return {{c->phase64, c->weight64}, c->tw64, c->inv_sig64, c->sk_sig64};
+  return {{c->phase64, c->weight64}, c->tw64, nullptr, c->inv_sig64, c->sk_sig64};
 }
 template <>
 inline NbarTabs<float> nbar_tabs<float>(const arp_ctx* c) {
-  return {{c->phase32, c->weight32}, c->tw32, c->inv_sig32, c->sk_sig32};
+  return {{c->phase32, c->weight32}, c->tw32, c->tw16_32, c->inv_sig32, c->sk_sig32};
 }
 
 template <typename T, int LOGN>

@@ -101,8 +101,9 @@ __device__ __forceinline__ void butterfly16_positions(int base, int at[16]) {
   for (int q = 0; q < 16; ++q) at[q] = E >= 16 ? (sb ^ ((q * E >> 4) & 15)) + q * E : sb ^ pidx16(q * E);
 }
 
-// One outer radix-16 stage of span L = 2^LOGL on the two lanes of one state
-// (lane l at Z + l N), one lane's butterfly per item: DIF (inverse, sign +):
+// One outer radix-16 stage of span L = 2^LOGL on the two lanes of each of
+// `nstates` states (state d's lane l at Z + (2d + l) N; the items of one state
+// are 2 N/16 consecutive ones), one lane's butterfly per item: DIF (inverse, sign +):
 // DFT then multiply by conj(tw); DIT (forward, sign -): multiply by tw, then
 // DFT; tw[(q-1) L/16 + j] = e^{-2 pi i q j / L}.  PRUNE 1: inputs q = 6..9 are
 // zero and not read; PRUNE 2: outputs q = 6..9 of lane 0 and q >= 6 of lane 1
@@ -110,13 +111,15 @@ __device__ __forceinline__ void butterfly16_positions(int base, int at[16]) {
 // GROUPED: warp w takes butterflies 16w .. 16w+15 of both lanes (one per
 // half-warp), which at span N/16 are the points 256w .. 256w+255.
 template <int N, int BLOCK, int SIGN, bool DIF, int LOGL, int PRUNE = 0, bool GROUPED = false>
-__device__ __forceinline__ void radix16_stage(cf* Z, const cf* tw) {
+__device__ __forceinline__ void radix16_stage(cf* Z, const cf* tw, int nstates = 1) {
   constexpr int NB = N / 16;
   constexpr int E = 1 << (LOGL - 4);
-  for (int item = threadIdx.x; item < 2 * NB; item += BLOCK) {
+  static_assert(BLOCK % (2 * NB) == 0 && (2 * NB) % 32 == 0, "whole states per block, whole warps per state");
+  for (int vitem = threadIdx.x; vitem < nstates * 2 * NB; vitem += BLOCK) {
+    const int d = vitem / (2 * NB), item = vitem - d * 2 * NB;
     const int lane = GROUPED ? (item >> 4) & 1 : item / NB;
     const int bidx = GROUPED ? ((item >> 5) << 4) | (item & 15) : item - lane * NB;
-    cf* Zl = Z + lane * N;
+    cf* Zl = Z + (2 * d + lane) * N;
     const int j = bidx & (E - 1);
     const int base = ((bidx >> (LOGL - 4)) << LOGL) + j;
     int at[16];
@@ -148,18 +151,22 @@ __device__ __forceinline__ void radix16_stage(cf* Z, const cf* tw) {
 }
 
 // The middle stage (span R = 2^(log2 N mod 4) = N/256, twiddles 1) on both
-// lanes: last inverse DFT, products, first forward DFT on the same R
-// positions.  With N/8 threads, warp w takes the items of points 256w ..
-// 256w+255, the points its own GROUPED span-N/16 stages read and write, so
-// only the warp synchronises around this stage.
+// lanes of each state: last inverse DFT, products, first forward DFT on the
+// same R positions.  Per state, the state's warp w (N/8 threads per state,
+// taken in the order of the radix-16 stages' items) takes the items of points
+// 256w .. 256w+255, the points its own GROUPED span-N/16 stages read and
+// write, so only the warp synchronises around this stage.
 template <int LOGN, int BLOCK>
-__device__ __forceinline__ void middle16_stage(cf* Z) {
+__device__ __forceinline__ void middle16_stage(cf* Z, int nstates = 1) {
   constexpr int N = 1 << LOGN;
   constexpr int R = 1 << r16_log_mid(LOGN);
-  static_assert(BLOCK == N / 8 && R == N / 256, "one warp per 256 points");
-  cf* Z0 = Z;
-  cf* Z1 = Z + N;
-  const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+  constexpr int ST = N / 8;  // threads per state
+  static_assert(BLOCK % ST == 0 && R == N / 256, "one warp per 256 points");
+  for (int vt = threadIdx.x; vt < nstates * ST; vt += BLOCK) {
+  const int d = vt / ST, tl = vt - d * ST;
+  cf* Z0 = Z + 2 * d * N;
+  cf* Z1 = Z0 + N;
+  const int w = tl >> 5, t = tl & 31;
 #pragma unroll
   for (int r = 0; r < 8 / R; ++r) {
     const int i = (256 / R) * w + t + 32 * r;
@@ -201,26 +208,30 @@ __device__ __forceinline__ void middle16_stage(cf* Z) {
       Z1[p0 ^ q] = b[q];
     }
   }
+  }
 }
 
-// Inverse transform, products and forward transform of one state's two lanes
-// (Z and Z + N; entry and exit synchronised).  TW: the radix-16 twiddle tables.
+// Inverse transform, products and forward transform of the two lanes of each
+// of `nstates` states (state d's lanes at Z + 2dN and Z + (2d+1)N; entry and
+// exit synchronised).  TW: the radix-16 twiddle tables.  BLOCK is a multiple
+// of N/8: a thread takes the same states, and within a state the same warp's
+// points, in the span-N/16 stages and the middle stage.
 template <int LOGN, int BLOCK>
-__device__ __forceinline__ void nonlinear_transform16(cf* Z, const cf* TW) {
+__device__ __forceinline__ void nonlinear_transform16(cf* Z, const cf* TW, int nstates = 1) {
   constexpr int N = 1 << LOGN;
   constexpr int MID = r16_log_mid(LOGN);
   static_assert(LOGN - 8 == MID, "two radix-16 stages and a middle stage");
-  static_assert(BLOCK == N / 8, "one radix-16 butterfly per thread");
-  radix16_stage<N, BLOCK, +1, true, LOGN, 1>(Z, TW + twiddle16_offset(LOGN, LOGN));
+  static_assert(BLOCK % (N / 8) == 0, "one radix-16 butterfly per thread and state");
+  radix16_stage<N, BLOCK, +1, true, LOGN, 1>(Z, TW + twiddle16_offset(LOGN, LOGN), nstates);
   __syncthreads();
   // span N/16, middle and span N/16 again touch each warp's own 256 points
-  radix16_stage<N, BLOCK, +1, true, LOGN - 4, 0, true>(Z, TW + twiddle16_offset(LOGN, LOGN - 4));
+  radix16_stage<N, BLOCK, +1, true, LOGN - 4, 0, true>(Z, TW + twiddle16_offset(LOGN, LOGN - 4), nstates);
   __syncwarp();
-  middle16_stage<LOGN, BLOCK>(Z);
+  middle16_stage<LOGN, BLOCK>(Z, nstates);
   __syncwarp();
-  radix16_stage<N, BLOCK, -1, false, LOGN - 4, 0, true>(Z, TW + twiddle16_offset(LOGN, LOGN - 4));
+  radix16_stage<N, BLOCK, -1, false, LOGN - 4, 0, true>(Z, TW + twiddle16_offset(LOGN, LOGN - 4), nstates);
   __syncthreads();
-  radix16_stage<N, BLOCK, -1, false, LOGN, 2>(Z, TW + twiddle16_offset(LOGN, LOGN));
+  radix16_stage<N, BLOCK, -1, false, LOGN, 2>(Z, TW + twiddle16_offset(LOGN, LOGN), nstates);
   __syncthreads();
 }
 
